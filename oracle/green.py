@@ -1,0 +1,87 @@
+"""Green preconditioner M^-1 = F^-1 G_hat F (paper Sec. 3.1, Eq. prec_lin_systemG_FFT, Alg. 1).
+
+Alg. 1, as read here:
+  Step 1: for each component alpha, apply K_ref (uniform reference material) to a
+          unit impulse in component alpha at node 0; the response is row alpha of
+          the impulse-response array R[alpha, beta, N_1..N_d].
+  Step 2: component-wise DFT of every R[alpha, beta]. (The printed loop range
+          "{0..d}^d" and the in-place transform of K_hat are read as (alpha, beta)
+          in {1..d}^2 and K_hat[alpha, beta] = F(R[alpha, beta]).)
+  Step 3: invert the d x d block at every frequency; the zero frequency block is
+          set to 0 (zero-mean constraint; the printed index [:, :, 1, 1, 1] is read
+          as "the zero frequency" for any d).
+
+DFT convention (unstated in the paper): unnormalised forward transform
+F[k] = sum_I x[I] exp(-2 pi i k.I / n), inverse with 1/N, i.e. numpy.fft.fftn /
+ifftn. With this convention (K u)_beta = F^-1( sum_alpha K_hat[alpha, beta] F(u_alpha) ),
+so the block acting on the vector of transformed components is K_hat^T; the
+oracle applies exactly that transpose (for the centrosymmetric Q1 stencil K_hat is
+real symmetric, so the transpose is immaterial, which a test asserts).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import assemble
+
+
+def impulse_responses(n, C_ref: np.ndarray) -> np.ndarray:
+    """Step 1 of Alg. 1: R[alpha, beta, *n] = (K_ref e_{alpha, node 0})_beta."""
+    n = tuple(int(k) for k in n)
+    d = len(n)
+    K_ref = assemble.assemble_K(n, np.ones(n), C_ref)
+    R = np.zeros((d, d) + n)
+    for alpha in range(d):
+        imp = np.zeros((d,) + n)
+        imp[(alpha,) + (0,) * d] = 1.0
+        R[alpha] = assemble.apply(K_ref, imp)
+    return R
+
+
+def dft(x: np.ndarray, axes, inverse: bool = False) -> np.ndarray:
+    """Explicit O(N^2) multidimensional DFT by dense matrices along each axis (small grids)."""
+    y = np.asarray(x, dtype=np.complex128)
+    for ax in axes:
+        m = y.shape[ax]
+        j = np.arange(m)
+        sign = 1.0 if inverse else -1.0
+        W = np.exp(sign * 2j * np.pi * np.outer(j, j) / m)
+        if inverse:
+            W = W / m
+        y = np.moveaxis(np.tensordot(W, np.moveaxis(y, ax, 0), axes=(1, 0)), 0, ax)
+    return y
+
+
+def _transform(x, axes, inverse, explicit):
+    if explicit:
+        return dft(x, axes, inverse)
+    return np.fft.ifftn(x, axes=axes) if inverse else np.fft.fftn(x, axes=axes)
+
+
+def green_symbol(n, C_ref: np.ndarray, explicit_dft: bool = False):
+    """Steps 2-3 of Alg. 1. Returns (K_hat, G_hat), each complex [d, d, *n]."""
+    n = tuple(int(k) for k in n)
+    d = len(n)
+    R = impulse_responses(n, C_ref)
+    axes = tuple(range(2, 2 + d))
+    K_hat = _transform(R, axes, False, explicit_dft)
+    blocks = np.moveaxis(K_hat.reshape(d, d, -1), 2, 0)  # [N, d, d]
+    G_blocks = np.zeros_like(blocks)
+    G_blocks[1:] = np.linalg.inv(blocks[1:])  # frequency 0 is flat index 0
+    G_hat = np.moveaxis(G_blocks, 0, 2).reshape((d, d) + n)
+    return K_hat, G_hat
+
+
+def apply_green(G_hat: np.ndarray, r: np.ndarray, explicit_dft: bool = False) -> np.ndarray:
+    """z = F^-1 G_hat F r for r of shape [d, *n] (the transpose reading above)."""
+    d = r.shape[0]
+    axes = tuple(range(1, 1 + d))
+    r_hat = _transform(r, axes, False, explicit_dft)
+    z_hat = np.einsum("ab...,a...->b...", G_hat, r_hat)
+    return _transform(z_hat, axes, True, explicit_dft).real
+
+
+def apply_green_jacobi(G_hat: np.ndarray, J_half: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """z = J^(1/2) F^-1 G_hat F J^(1/2) r (paper Eq. prec_lin_systemJG_2)."""
+    return J_half * apply_green(G_hat, J_half * r)
