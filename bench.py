@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 J-FFT solver on the 2D 1024 x 1024 workload.
+
+Workload (one "step" = one pass of the whole path over the sweep):
+  2D plane-strain periodic cell, 1024 x 1024 bilinear quads with 4 Gauss points, FP64;
+  density from 16 random Fourier modes with |k| <= 8 (seed 0), affinely mapped to
+  [0, 1]; E = E_min + (1 - E_min) rho^2 with contrast 1/E_min in {1e2, 1e4, 1e6};
+  nu = 0.3; C_ref = mean material; the three Mandel unit load cases, solved as one
+  batch with per-load convergence; Green-Jacobi and Green; relative residual 1e-8.
+  Per contrast: material setup (E, J^1/2, Alg. 1 symbol) + one Green-Jacobi solve
+  and one Green solve of the three loads -> 18 PCG solves per step.
+
+value: solves/s with the density field resident in HBM and outputs written to
+device buffers; e2e: the same through the C ABI with host buffers (pinned), the
+host->device copy of the density and the device->host read of u, C_hom, iteration
+counts and residuals inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path has no
+exchange step), rank 0 prints one JSON line with the max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SHAPE = (1024, 1024)
+MODES, KMAX, SEED = 16, 8.0, 0
+EXPONENT, NU, TOL = 2.0, 0.3, 1e-8
+CONTRASTS = (1e2, 1e4, 1e6)
+PRECONDS = ("green_jacobi", "green")
+N_LOADS = 3
+METRIC = "PCG solves/s"
+WORKLOAD = ("2D plane-strain periodic cell, 1024x1024 Q1 quads (4 Gauss points), FP64; smooth density "
+            "(16 Fourier modes, |k|<=8), E = 1/c + (1-1/c) rho^2, c in {1e2,1e4,1e6}, nu 0.3, C_ref mean; "
+            "3 Mandel unit loads; Green-Jacobi and Green PCG to 1e-8 relative residual")
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # SMs x max clock x FP64 flop/clk/SM (2 DFMA)
+ITER_COUNTS = os.path.join(ROOT, "oracle", "data", "iters_2d_1024.json")
+
+
+# ----------------------------------------------------------------- helpers
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def flops_per_unit(kernel, shape, d=2):
+    """Algorithmic FLOPs of one kernel for one load case (one right-hand side).
+
+    FFT passes use the conventional 5 L log2 L per complex transform of length L
+    (2.5 n log2 n for a real transform of length n); the symbol block multiply of a
+    real symmetric d x d block by a complex vector costs 2 d^2 mults + 2 d (d-1)
+    adds per frequency; J^1/2 scalings one multiply per real value. The Q1 operator
+    counts the flops of its Walsh-Hadamard mode form (74 per node in 2D, see the
+    design notes), FMA = 2 flops."""
+    n0, n1 = shape
+    N = n0 * n1
+    M = n1 // 2
+    F = n0 * (M + 1)
+    if kernel == "fft_lines":
+        return d * (M + 1) * 2 * 5 * n0 * math.log2(n0) + F * (2 * d * d * 2 + 2 * d * (d - 1))
+    if kernel == "fft_rows_real_fwd":
+        return d * n0 * 2.5 * n1 * math.log2(n1) + d * N          # + J^1/2 scaling
+    if kernel == "fft_cols_real_inv":
+        return d * n0 * 2.5 * n1 * math.log2(n1) + 3 * d * N      # + J^1/2 scaling and r.z
+    if kernel == "apply_K":
+        return 74 * N + 2 * d * N                                  # operator + fused p.q
+    return None
+
+
+def traffic_bytes_per_unit(kernel, shape, d=2):
+    """Compulsory DRAM bytes of one kernel for one load case (FP64)."""
+    n0, n1 = shape
+    N = n0 * n1
+    F = n0 * (n1 // 2 + 1)
+    if kernel == "fft_lines":
+        return 2 * d * F * 16 + F * 3 * 8                          # spectrum in+out, symbol table
+    if kernel == "fft_rows_real_fwd":
+        return d * N * 8 + d * F * 16 + N * 8
+    if kernel == "fft_cols_real_inv":
+        return d * F * 16 + 2 * d * N * 8 + N * 8
+    if kernel == "apply_K":
+        return 2 * d * N * 8 + N * 8
+    return None
+
+
+# ----------------------------------------------------------------- CPU side
+def cpu_sample(seconds_budget=25.0):
+    """Time the oracle as it stands on a bounded sample of the workload (single process).
+
+    Sample: oracle setup (assembled sparse K, Alg. 1 symbol, diagonal) at 1024 x 1024
+    for contrast 1e4, the right-hand side and post-processing of one load, and a few
+    Green-Jacobi and Green PCG iterations on that load."""
+    from oracle import assemble, material, pcg, post, solve as osolve
+    from synthetic import smooth_density
+    rho = smooth_density(SHAPE, MODES, KMAX, SEED)
+    E = material.young_from_density(rho, 1e-4, 1.0, EXPONENT)
+    t0 = time.perf_counter()
+    prob = osolve.setup(SHAPE, E, NU)
+    t_setup = time.perf_counter() - t0
+    eps = np.eye(3)[0]
+    t0 = time.perf_counter()
+    f = assemble.assemble_rhs(SHAPE, E, prob.C, eps)
+    t_rhs = time.perf_counter() - t0
+    per_it = {}
+    for pc in PRECONDS:
+        k = 3
+        t0 = time.perf_counter()
+        res = pcg.pcg(prob.apply_K, prob.minv(pc), f, 0.0, k)
+        per_it[pc] = (time.perf_counter() - t0) / k
+    t0 = time.perf_counter()
+    u = post.remove_mean(res.x)
+    post.element_stress(SHAPE, E, prob.C, eps, u)
+    post.homogenised_stress(SHAPE, E, prob.C, eps, u)
+    np.linalg.norm(f - prob.apply_K(u))
+    t_post = time.perf_counter() - t0
+    return {"t_setup": t_setup, "t_rhs": t_rhs, "t_iter": per_it, "t_post": t_post}
+
+
+def cpu_extrapolate(sample, iters):
+    """Seconds for one step (the 18 solves) from the sampled costs and iteration counts
+    iters[(contrast, precond)] = list of per-load counts."""
+    total = len(CONTRASTS) * sample["t_setup"]
+    for (c, pc), its in iters.items():
+        total += sum(sample["t_rhs"] + n * sample["t_iter"][pc] + sample["t_post"] for n in its)
+    return total
+
+
+def oracle_iteration_counts():
+    with open(ITER_COUNTS) as fh:
+        rows = json.load(fh)["solves"]
+    out = {}
+    for r in rows:
+        out.setdefault((r["contrast"], r["precond"]), [0, 0, 0])[r["load"]] = r["iters"]
+    return out
+
+
+def run_cpu_sample_subprocess():
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = "import json, bench; print('CPUSAMPLE ' + json.dumps(bench.cpu_sample()))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                       stderr=subprocess.PIPE, text=True, timeout=900)
+    for line in r.stdout.splitlines():
+        if line.startswith("CPUSAMPLE "):
+            return json.loads(line[len("CPUSAMPLE "):])
+    raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------- reference arm
+def reference_arm(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    iters = oracle_iteration_counts()
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; samples below are independent
+    secs = []
+    samples = []
+    for _ in range(args.steps):
+        s = run_cpu_sample_subprocess()
+        samples.append(s)
+        secs.append(cpu_extrapolate(s, iters))
+    step_s = statistics.mean(secs)
+    value = len(CONTRASTS) * len(PRECONDS) * N_LOADS / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "contrasts": list(CONTRASTS),
+                   "preconditioners": list(PRECONDS), "loads": N_LOADS, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": ("per step: oracle setup at 1024x1024 (contrast 1e4), one load's rhs and "
+                                    "post-processing, 3 Green-Jacobi and 3 Green iterations; scaled to the 18 "
+                                    "solves with the oracle's own iteration counts (oracle/data/iters_2d_1024.json)"),
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    global CONTRASTS, PRECONDS
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--contrasts", default=",".join(f"{c:g}" for c in CONTRASTS),
+                    help="subset of the contrast sweep (profiling runs)")
+    ap.add_argument("--preconds", default=",".join(PRECONDS), help="subset of the preconditioners (profiling runs)")
+    args = ap.parse_args()
+    CONTRASTS = tuple(float(c) for c in args.contrasts.split(","))
+    PRECONDS = tuple(args.preconds.split(","))
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_sample_subprocess()   # before any CUDA call in this process
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_02613_gb300.jfft import Solver
+    from synthetic import smooth_density
+
+    stream = torch.cuda.current_stream()
+    rho_h = smooth_density(SHAPE, MODES, KMAX, SEED)
+    rho_d = torch.tensor(rho_h, device="cuda")
+    eps_h = np.eye(3)
+    eps_d = torch.tensor(eps_h, device="cuda")
+    s = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
+               stream=stream.cuda_stream, io="device", max_loads=N_LOADS)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def step(record=None):
+        for c in CONTRASTS:
+            s.set_material(rho_d, e_min=1.0 / c)
+            for pc in PRECONDS:
+                out = s.solve(eps_d, TOL, pc, want_stress=False)
+                if record is not None:
+                    record[(c, pc)] = [int(v) for v in out["iters"].cpu().tolist()]
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    iters = {}
+    step(iters)            # untimed pass that records iteration counts
+    barrier()
+    uuid = str(getattr(torch.cuda.get_device_properties(local), "uuid", ""))
+    clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or local))
+    clocks.start()
+    s.set_profiling(True)
+    n_launch0 = s.launch_count
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)   # L2 flush (256 MiB > 129 MB L2), outside the timed interval
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1))
+    launches = s.launch_count - n_launch0
+    prof = s.profile()
+    s.set_profiling(False)
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    solves_per_step = len(CONTRASTS) * len(PRECONDS) * N_LOADS
+    value = world * solves_per_step / (ms / 1e3)
+
+    # ---- e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        sh = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
+                    stream=stream.cuda_stream, io="host", max_loads=N_LOADS, pinned=True)
+        rho_pin = torch.empty(SHAPE, dtype=torch.float64, pin_memory=True).numpy()
+        rho_pin[...] = rho_h
+        h2d = d2h = 0
+
+        def step_host():
+            nonlocal h2d, d2h
+            for c in CONTRASTS:
+                sh.set_material(rho_pin, e_min=1.0 / c)
+                h2d += rho_pin.nbytes
+                for pc in PRECONDS:
+                    out = sh.solve(eps_h, TOL, pc, want_stress=False)
+                    h2d += eps_h.nbytes
+                    d2h += out["u"].nbytes + out["C_hom"].nbytes + out["iters"].nbytes + out["rel_res"].nbytes
+
+        for _ in range(3):
+            step_host()
+        barrier()
+        h2d = d2h = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        barrier()
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * solves_per_step / t_e2e, "unit": "solves/s",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+        sh.close()
+
+    # ---- roofline of the dominant kernel (CUDA events around each launch, timed region)
+    units = {}  # right-hand-side applications per kernel over the timed region
+    n_pc = sum(sum(v) for v in iters.values())  # preconditioner and CG-operator applications per step
+    units["fft_lines"] = units["fft_rows_real_fwd"] = units["fft_cols_real_inv"] = units["apply_K"] = \
+        n_pc * args.steps
+    roof = None
+    rows = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda r: -r[2])
+    total_ms = sum(r[2] for r in rows)
+    for name, nl, tot in rows:
+        fl = flops_per_unit(name, SHAPE)
+        if fl is None:
+            continue
+        achieved = units[name] * fl / (tot / 1e3) / 1e12
+        byt = traffic_bytes_per_unit(name, SHAPE)
+        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
+                "algorithmic_bytes_per_unit": byt,
+                "hbm_GBps_algorithmic": units[name] * byt / (tot / 1e3) / 1e9,
+                "peak_note": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (probe measured 1.197 TFLOP/s DFMA)"}
+        break
+
+    cpu_line = None
+    if cpu is not None:
+        cpu_step = cpu_extrapolate(cpu, {k: v for k, v in iters.items()})
+        cpu_line = {"value": solves_per_step / cpu_step, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                    "sample": ("oracle setup at 1024x1024 (contrast 1e4), one load's rhs and post-processing, "
+                               "3 Green-Jacobi and 3 Green iterations, scaled to this step's 18 solves with the "
+                               "GPU run's iteration counts"),
+                    "cpu": cpu_model(), "sample_seconds": cpu}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "contrasts": list(CONTRASTS),
+                       "preconditioners": list(PRECONDS), "loads": N_LOADS, "tol": TOL,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MiB buffer written before each timed step (outside the timed interval)"},
+            "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": launches // args.steps,
+            "clocks": clk,
+            "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
+                       "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()},
+                       "kernel_launches": {k: v[0] for k, v in prof.items()},
+                       "step_ms": times},
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * jfft.h -- C ABI of the GB300 J-FFT solver.
+ *
+ * Solves the periodic small-strain linear-elastic cell problem on a regular grid
+ * (Ladecky et al., arXiv 2508.02613, Sec. 2) with preconditioned conjugate
+ * gradients (Sec. 2.3) and the Green (Sec. 3.1, Eq. prec_lin_systemG_FFT), Jacobi
+ * (Sec. 3.2, Eq. prec_lin_systemJ) or Green-Jacobi preconditioner (Sec. 3.3,
+ * Eq. prec_lin_systemJG_2). The discretisation is Q1 (bilinear quads with 2x2 Gauss
+ * points in 2D, plane strain; trilinear hexes with 2x2x2 Gauss points in 3D) on the
+ * unit cell with n_a nodal points per axis, periodic, h_a = 1 / n_a (Sec. 2.1).
+ *
+ * Conventions shared by every call:
+ *  - Node I = (i_1, .., i_d) has flat index ((i_1 n_2) + i_2) n_3 + i_3 (C order,
+ *    last axis contiguous); N = n_1 ... n_d. Voxel (element) e has its lowest
+ *    corner at node e and couples nodes (e + o) mod n, o in {0,1}^d.
+ *  - A displacement-like field is an array [d][N] of doubles (component-major,
+ *    the [d, N_1, .., N_d] layout of the paper's Alg. 1). Several fields are
+ *    stacked as [count][d][N].
+ *  - Strain and stress use Mandel notation: 2D (11, 22, sqrt2*12); 3D
+ *    (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12) (Sec. 2; sqrt2 as in Sec. 4.5).
+ *  - Material: C_e = E_e * C_unit(nu), isotropic, unit Young's modulus, plane
+ *    strain in 2D (the paper's sigma = rho C^0 eps of Sec. 4 has this form).
+ *  - Data pointers passed to any call other than jfft_create are host pointers
+ *    when the handle's io memory is JFFT_MEM_HOST (default) and device pointers
+ *    (on the handle's device) when it is JFFT_MEM_DEVICE; this includes the
+ *    material field given to jfft_set_material. The field given to jfft_create is
+ *    always a host pointer. The caller owns
+ *    every buffer it passes; inputs are read during the call only, outputs are
+ *    written before the call returns (device outputs: ordered on the handle's
+ *    stream, complete when the call returns because each call synchronises it).
+ *  - Every call returns a jfft_status; on failure jfft_last_error() returns a
+ *    message. A handle is not thread safe; distinct handles are independent.
+ *  - The library allocates its device workspace with the CUDA runtime inside
+ *    jfft_create and frees it in jfft_destroy.
+ */
+#ifndef JFFT_H
+#define JFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JFFT_API_VERSION 1
+
+typedef struct jfft_solver jfft_solver; /* opaque; owns all device memory */
+
+typedef enum {
+  JFFT_OK = 0,
+  JFFT_ERR_ARG = 1,          /* invalid argument (message says which) */
+  JFFT_ERR_OOM = 2,          /* workspace does not fit the device or the hbm_budget */
+  JFFT_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  JFFT_ERR_NOCONV = 4,       /* max_iter reached; outputs hold the last iterate */
+  JFFT_ERR_BREAKDOWN = 5,    /* p.Kp <= 0 or a non-finite CG scalar; outputs hold the last iterate */
+  JFFT_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  JFFT_ERR_UNSUPPORTED = 7   /* valid request outside what this build implements */
+} jfft_status;
+
+typedef enum {
+  JFFT_PC_NONE = -1,         /* plain CG (M = I), for testing */
+  JFFT_PC_GREEN = 0,         /* M^-1 = F^-1 G_hat F (Eq. prec_lin_systemG_FFT) */
+  JFFT_PC_GREEN_JACOBI = 1,  /* M^-1 = J^1/2 F^-1 G_hat F J^1/2 (Eq. prec_lin_systemJG_2) */
+  JFFT_PC_JACOBI = 2         /* M^-1 = diag(K)^-1 (Eq. prec_lin_systemJ) */
+} jfft_precond;
+
+typedef enum {
+  JFFT_MAT_YOUNG = 0,        /* field = E per voxel (>= 0, finite) */
+  JFFT_MAT_DENSITY = 1       /* field = rho per voxel; E = e_min + (e_max - e_min) rho^exponent, on the device */
+} jfft_material_kind;
+
+typedef enum { JFFT_PREC_FP64 = 0 } jfft_precision;
+
+typedef enum {
+  JFFT_STOP_REL = 0,         /* ||r_k||_2 <= tol ||f||_2 (r the recursively updated residual) */
+  JFFT_STOP_ABS_SQ = 1       /* ||r_k||_2^2 <= tol (the paper's rule, Sec. 4 "Termination criteria") */
+} jfft_stop_mode;
+
+typedef enum { JFFT_MEM_HOST = 0, JFFT_MEM_DEVICE = 1 } jfft_memory;
+
+typedef enum {
+  JFFT_DIAG_CLOSED_FORM = 0, /* diag(K)_{aI} = kappa_a * sum of E over the 2^d voxels at node I */
+  JFFT_DIAG_COMBS = 1        /* Alg. 2: d 2^d operator applications to impulse combs (even n only) */
+} jfft_diag_method;
+
+typedef struct {
+  int dim;                   /* 2 or 3 */
+  int64_t n[3];              /* nodal points (= voxels) per axis; each a power of two, 4..2048 (2D), 4..1024 (3D) */
+} jfft_grid;
+
+typedef struct {
+  int kind;                  /* jfft_material_kind */
+  const double* field;       /* array [N] in node order (voxel e at its lowest-corner node) */
+  double nu;                 /* Poisson ratio, -1 < nu < 0.5 */
+  double e_min, e_max;       /* JFFT_MAT_DENSITY only */
+  double exponent;           /* JFFT_MAT_DENSITY only (> 0) */
+} jfft_material;
+
+typedef struct {
+  int precision;             /* jfft_precision (FP64) */
+  int max_iter;              /* PCG iteration cap per load case (default 100000) */
+  int stop_mode;             /* jfft_stop_mode (default JFFT_STOP_REL) */
+  void* stream;              /* cudaStream_t to run on; NULL = the legacy default stream */
+  size_t hbm_budget;         /* bytes the workspace may take; 0 = no limit beyond free memory */
+  int check_every;           /* PCG iterations launched between host convergence checks (default 8) */
+  int io_memory;             /* jfft_memory for the data pointers of later calls (default HOST) */
+  int max_loads;             /* largest n_loads / count accepted by later calls (default 6) */
+  double void_value;         /* replaces zero diagonal entries of K before J = diag^-1 (default 1, Sec. 3.2) */
+  int device;                /* CUDA device ordinal (default 0) */
+} jfft_options;
+
+typedef struct {
+  double* u;                 /* [n_loads][d][N] zero-mean fluctuation displacement, or NULL */
+  double* stress;            /* [n_loads][d*][N] element-averaged Mandel stress, or NULL */
+  double* C_hom;             /* [d*][n_loads]: column g = cell-averaged stress for eps_bar[g], or NULL */
+  int* iters;                /* [n_loads] PCG iterations (operator applications in the loop), or NULL */
+  double* rel_res;           /* [n_loads] true ||f - K u||_2 / ||f||_2 recomputed at exit (0 if f = 0), or NULL */
+} jfft_result;
+
+/* Fill *opt with the defaults listed above. */
+void jfft_default_options(jfft_options* opt);
+
+/*
+ * Create a solver for one grid and material (paper Sec. 2-3; setup steps of
+ * Alg. 1 and Alg. 2). Uploads the field, computes E (Sec. 4 "Constitutive law"),
+ * the reference symbol G_hat by Alg. 1 on the device (impulse responses of K_ref,
+ * forward FFT, d x d inversion, zero frequency pinned to 0) and J^1/2 with the
+ * void rule (Sec. 3.2). C_ref: NULL selects mean(E) C_unit(nu) (the mean
+ * material); otherwise a host [d*][d*] Mandel matrix that must be isotropic
+ * (lambda, mu with mu > 0, lambda + 2 mu / d > 0), else JFFT_ERR_UNSUPPORTED.
+ * opt may be NULL (defaults). On success *out is a new handle; on failure *out
+ * is NULL and the returned status says why.
+ */
+jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, const jfft_material* mat,
+                        const double* C_ref, const jfft_options* opt);
+
+/* Replace the material field (same grid, nu and C_ref choice); recomputes E,
+ * J^1/2 and, when C_ref was NULL, G_hat for the new mean (Alg. 1). No
+ * reallocation. The field pointer follows the handle's io memory; a device field
+ * is validated on the device (JFFT_ERR_ARG if any entry is negative or not finite). */
+jfft_status jfft_set_material(jfft_solver* h, const jfft_material* mat);
+
+/*
+ * Solve for n_loads macroscopic strains eps_bar [n_loads][d*] (Mandel): for each,
+ * f = -B^T W C eps_bar (Eq. lin_system_exp), PCG from u_0 = 0 (Sec. 4 "Initial
+ * solution") until the stop rule with tolerance tol, then the post-processing of
+ * Sec. 5.3 / Eq. aim_fun (mean removal, stresses, homogenised stiffness) and the
+ * true relative residual. The load cases run as one batch with per-load
+ * convergence. JFFT_ERR_NOCONV / JFFT_ERR_BREAKDOWN still fill the outputs.
+ */
+jfft_status jfft_solve(jfft_solver* h, int n_loads, const double* eps_bar, double tol,
+                       int precond, jfft_result* res);
+
+/* Free the handle and its device memory. NULL is ignored. */
+void jfft_destroy(jfft_solver* h);
+
+const char* jfft_status_string(jfft_status s);
+/* Message of the last failure on h; with h == NULL, the message of the last
+ * failed jfft_create on the calling thread. Valid until the next call. */
+const char* jfft_last_error(const jfft_solver* h);
+
+/* Per-handle settings. */
+jfft_status jfft_set_io_memory(jfft_solver* h, int io_memory);
+jfft_status jfft_set_max_iter(jfft_solver* h, int max_iter);
+
+/* ---- building blocks of the path (same handle, same pointer rules) ---- */
+
+/* S1: the per-voxel Young's modulus E [N] as used by the solver. */
+jfft_status jfft_get_material(jfft_solver* h, double* E);
+
+/* S2: f = -B^T W C eps_bar for count strains [count][d*] -> f [count][d][N] (Eq. lin_system_exp). */
+jfft_status jfft_rhs(jfft_solver* h, int count, const double* eps_bar, double* f);
+
+/* S3: y = K x for count fields [count][d][N], K = B^T W C B matrix free (Sec. 3.1 "Matrix-free assembly"). */
+jfft_status jfft_apply_K(jfft_solver* h, int count, const double* x, double* y);
+
+/* S5: diag(K) [d][N] before the void rule, by the closed form or by Alg. 2. */
+jfft_status jfft_get_diag(jfft_solver* h, int method, double* diag);
+
+/*
+ * S9: the Green symbol G_hat of Alg. 1 on the half spectrum. Output [F][d][d]
+ * (row-major d x d block per frequency), frequencies ordered with k_1 fastest:
+ * 2D index (k_2 * n_1 + k_1), 3D ((k_3 * n_2 + k_2) * n_1 + k_1), with
+ * 0 <= k_d <= n_d / 2 on the last (contiguous) axis and 0 <= k_a < n_a elsewhere;
+ * F = n_1 .. n_{d-1} (n_d / 2 + 1). Values are the inverse of K_hat_ref (the
+ * unnormalised DFT of the impulse responses), zero at k = 0.
+ */
+jfft_status jfft_get_green(jfft_solver* h, double* G);
+
+/* S5 + S6: z = M^-1 r for count fields [count][d][N] and the given preconditioner. */
+jfft_status jfft_apply_precond(jfft_solver* h, int precond, int count, const double* r, double* z);
+
+/*
+ * S4 + S7: PCG for count arbitrary right-hand sides f [count][d][N] from u_0 = 0.
+ * u [count][d][N] receives the raw iterate (no mean removal), iters [count] the
+ * iteration counts. With tol = 0 exactly max_iter iterations run (same-k tests).
+ */
+jfft_status jfft_solve_rhs(jfft_solver* h, int count, const double* f, double tol, int precond,
+                           double* u, int* iters);
+
+/* S8: for count strains and displacements u [count][d][N] (used as given), the
+ * element-averaged stress [count][d*][N] and C_hom [d*][count]; either may be NULL. */
+jfft_status jfft_postprocess(jfft_solver* h, int count, const double* eps_bar, const double* u,
+                             double* stress, double* C_hom);
+
+/* ---- instrumentation ---- */
+
+/* Number of kernels this handle has launched since creation. */
+int64_t jfft_launch_count(const jfft_solver* h);
+
+/* When on, every kernel launch is bracketed by CUDA events on the handle's stream
+ * and accumulated per kernel name; jfft_profile_json returns
+ * {"kernel": [launches, total_ms], ...} (valid until the next call on h). */
+jfft_status jfft_set_profiling(jfft_solver* h, int on);
+const char* jfft_profile_json(jfft_solver* h);
+
+/* Bytes of device workspace this handle holds. */
+size_t jfft_workspace_bytes(const jfft_solver* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JFFT_H */

@@ -1,0 +1,821 @@
+// C ABI of the J-FFT solver (include/jfft.h): handle lifecycle, device workspace,
+// setup (material S1, Jacobi S5, Green symbol S9 by Alg. 1 on the device), the PCG
+// driver (S2-S7) and post-processing (S8).
+#include "jfft.h"
+#include "element.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace jfft;
+
+struct jfft_solver {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  Grid g = {};
+  int ds = 3;
+  jfft_options opt = {};
+  int io = JFFT_MEM_HOST;
+  int max_iter = 100000;
+  int max_loads = 6;
+  double nu = 0.3;
+  ElemConst ec = {};      // unit material C_unit(nu)
+  ElemConst ec_ref = {};  // reference material C_ref
+  bool cref_mean = true;
+  double cref_lam = 0.0, cref_mu = 0.0;
+  double e_ref = 1.0;
+  double kappa[3] = {0, 0, 0}, jscale[3] = {0, 0, 0}, void_js = 1.0;
+  double scale_store = 1.0;
+  // device workspace
+  double *field = nullptr, *E = nullptr, *esum = nullptr, *js = nullptr, *G = nullptr;
+  double2* tw[3] = {nullptr, nullptr, nullptr};
+  double2 *T = nullptr, *U = nullptr;
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
+  double *partial = nullptr, *red = nullptr;
+  CgState* cg = nullptr;
+  StrainShift* shifts = nullptr;
+  std::vector<void*> allocs;
+  // pinned host mirrors
+  CgState* cg_h = nullptr;
+  double* red_h = nullptr;
+  size_t ws_bytes = 0;
+  std::string err;
+  int64_t launches = 0;
+  bool profiling = false;
+  struct Pend { const char* name; cudaEvent_t a, b; };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<int64_t, double>> prof;
+  std::string prof_json;
+};
+
+// ------------------------------------------------------------- launch hooks
+static thread_local jfft_solver* g_cur = nullptr;
+static thread_local std::string g_create_err;  // message of the last failed jfft_create
+
+namespace jfft {
+void hook_begin(const char* name, cudaStream_t st) {
+  jfft_solver* h = g_cur;
+  if (!h) return;
+  h->launches++;
+  if (!h->profiling) return;
+  jfft_solver::Pend pe;
+  pe.name = name;
+  for (int i = 0; i < 2; ++i) {
+    cudaEvent_t ev;
+    if (!h->pool.empty()) { ev = h->pool.back(); h->pool.pop_back(); }
+    else cudaEventCreate(&ev);
+    (i == 0 ? pe.a : pe.b) = ev;
+  }
+  cudaEventRecord(pe.a, st);
+  h->pend.push_back(pe);
+}
+void hook_end(const char* /*name*/, cudaStream_t st) {
+  jfft_solver* h = g_cur;
+  if (!h || !h->profiling || h->pend.empty()) return;
+  cudaEventRecord(h->pend.back().b, st);
+}
+}  // namespace jfft
+
+struct CurGuard {
+  jfft_solver* prev;
+  explicit CurGuard(jfft_solver* h) : prev(g_cur) { g_cur = h; if (h) cudaSetDevice(h->device); }
+  ~CurGuard() { g_cur = prev; }
+};
+
+static void drain_profile(jfft_solver* h) {
+  for (auto& pe : h->pend) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+      auto& e = h->prof[pe.name];
+      e.first += 1;
+      e.second += ms;
+    }
+    h->pool.push_back(pe.a);
+    h->pool.push_back(pe.b);
+  }
+  h->pend.clear();
+}
+
+// ------------------------------------------------------------- helpers
+static jfft_status fail(jfft_solver* h, jfft_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+static jfft_status cuda_fail(jfft_solver* h, cudaError_t e, const char* where) {
+  return fail(h, JFFT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2i(int64_t v) { int l = 0; while ((int64_t(1) << l) < v) ++l; return l; }
+
+static jfft_status sync(jfft_solver* h) {
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  if (h->profiling) drain_profile(h);
+  return JFFT_OK;
+}
+
+static int64_t field_elems(const jfft_solver* h) { return (int64_t)h->g.d * h->g.N; }
+
+// copy count fields into / out of a device buffer according to the io mode
+static jfft_status copy_in(jfft_solver* h, double* dst, const double* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), h->io == JFFT_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                              : cudaMemcpyHostToDevice, h->st));
+  return JFFT_OK;
+}
+static jfft_status copy_out(jfft_solver* h, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, h->io == JFFT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->st));
+  return JFFT_OK;
+}
+
+static void isotropic_mandel(int d, double lam, double mu, double* C) {
+  const int ds = d * (d + 1) / 2;
+  for (int i = 0; i < ds * ds; ++i) C[i] = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) C[a * ds + b] = lam + (a == b ? 2.0 * mu : 0.0);
+  for (int s = d; s < ds; ++s) C[s * ds + s] = 2.0 * mu;
+}
+
+// ------------------------------------------------------------- lifecycle
+extern "C" void jfft_default_options(jfft_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = JFFT_PREC_FP64;
+  o->max_iter = 100000;
+  o->stop_mode = JFFT_STOP_REL;
+  o->stream = nullptr;
+  o->hbm_budget = 0;
+  o->check_every = 8;
+  o->io_memory = JFFT_MEM_HOST;
+  o->max_loads = 6;
+  o->void_value = 1.0;
+  o->device = 0;
+}
+
+static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
+  CK(cudaMalloc(ptr, bytes));
+  h->allocs.push_back(*ptr);
+  h->ws_bytes += bytes;
+  return JFFT_OK;
+}
+
+static void free_all(jfft_solver* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->cg_h) cudaFreeHost(h->cg_h);
+  if (h->red_h) cudaFreeHost(h->red_h);
+  h->cg_h = nullptr;
+  h->red_h = nullptr;
+  for (auto& pe : h->pend) { h->pool.push_back(pe.a); h->pool.push_back(pe.b); }
+  for (auto ev : h->pool) cudaEventDestroy(ev);
+  h->pool.clear();
+  h->pend.clear();
+}
+
+static jfft_status validate_material(jfft_solver* h, const jfft_material* m, int64_t N, bool field_on_device = false) {
+  if (!m || !m->field) return fail(h, JFFT_ERR_ARG, "material or material field is NULL");
+  if (m->kind != JFFT_MAT_YOUNG && m->kind != JFFT_MAT_DENSITY) return fail(h, JFFT_ERR_ARG, "unknown material kind");
+  if (!(m->nu > -1.0 && m->nu < 0.5)) return fail(h, JFFT_ERR_ARG, "Poisson ratio must lie in (-1, 0.5)");
+  if (m->kind == JFFT_MAT_DENSITY) {
+    if (!(std::isfinite(m->e_min) && std::isfinite(m->e_max) && m->e_min >= 0.0 && m->e_max >= m->e_min))
+      return fail(h, JFFT_ERR_ARG, "density material needs finite 0 <= e_min <= e_max");
+    if (!(m->exponent > 0.0 && std::isfinite(m->exponent))) return fail(h, JFFT_ERR_ARG, "exponent must be > 0");
+  }
+  if (field_on_device) return JFFT_OK;  // checked on the device after the copy
+  for (int64_t i = 0; i < N; ++i) {
+    const double v = m->field[i];
+    if (!std::isfinite(v) || v < 0.0) return fail(h, JFFT_ERR_ARG, "material field must be finite and >= 0");
+  }
+  return JFFT_OK;
+}
+
+// Alg. 1 on the device: impulse responses of K_ref, forward transform, inversion.
+static jfft_status build_symbol(jfft_solver* h) {
+  const Grid& g = h->g;
+  CK(launch_impulses(g, h->x, h->st));
+  CK(launch_apply_K(g, h->ec_ref, nullptr, 1.0, h->x, h->z, g.d, field_elems(h), nullptr, 1.0, 0, nullptr, nullptr,
+                    nullptr, h->st));
+  FftPlan pl = {{h->tw[0], h->tw[1], h->tw[2]}, h->T, h->U, h->G};
+  const double2* spec = nullptr;
+  CK(launch_forward_spectrum(g, pl, h->z, g.d, &spec, h->st));
+  CK(launch_green_table(g, spec, h->G, h->scale_store, h->st));
+  return JFFT_OK;
+}
+
+static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool field_on_device) {
+  const Grid& g = h->g;
+  jfft_status s = validate_material(h, m, g.N, field_on_device);
+  if (s) return s;
+  if (m->nu != h->nu) return fail(h, JFFT_ERR_ARG, "the Poisson ratio is fixed at creation");
+  CK(cudaMemcpyAsync(h->field, m->field, g.N * sizeof(double),
+                     field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  if (field_on_device) {
+    int* bad = reinterpret_cast<int*>(h->red);
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), h->st));
+    CK(launch_check_field(h->field, g.N, bad, h->st));
+    int bad_h = 0;
+    CK(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    s = sync(h);
+    if (s) return s;
+    if (bad_h) return fail(h, JFFT_ERR_ARG, "material field must be finite and >= 0");
+  }
+  CK(launch_material(h->field, h->E, g.N, m->kind, m->e_min, m->e_max, m->exponent, h->st));
+  CK(launch_node_esum(g, h->E, h->esum, h->st));
+  CK(launch_jacobi_half(h->esum, h->js, g.N, h->st));
+  double lam, mu;
+  if (h->cref_mean) {
+    int np = 0;
+    CK(launch_row_sums(h->E, 1, g.N, h->partial, &np, h->st));
+    CK(launch_reduce_partials(h->partial, np, 1, kMaxPartials, h->red, h->st));
+    CK(cudaMemcpyAsync(h->red_h, h->red, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    s = sync(h);
+    if (s) return s;
+    const double mean = h->red_h[0] / (double)g.N;
+    if (!(mean > 0.0)) return fail(h, JFFT_ERR_ARG, "mean(E) is zero: the mean reference material is undefined");
+    h->e_ref = mean;
+    lam = mean * h->ec.lam;
+    mu = mean * h->ec.mu;
+  } else {
+    lam = h->cref_lam;
+    mu = h->cref_mu;
+  }
+  double hh[3];
+  for (int a = 0; a < g.d; ++a) hh[a] = 1.0 / g.n[a];
+  h->ec_ref = make_elem_const(g.d, hh, lam, mu);
+  s = build_symbol(h);
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, const jfft_material* mat,
+                                   const double* C_ref, const jfft_options* opt) {
+  if (!out) return JFFT_ERR_ARG;
+  *out = nullptr;
+  jfft_solver* h = new jfft_solver();
+  CurGuard guard(nullptr);
+  auto bail = [&](jfft_status s) {
+    g_create_err = h->err.empty() ? jfft_status_string(s) : h->err;
+    free_all(h);
+    delete h;
+    return s;
+  };
+  jfft_options o;
+  jfft_default_options(&o);
+  if (opt) o = *opt;
+  h->opt = o;
+  if (!grid) return bail(fail(h, JFFT_ERR_ARG, "grid is NULL"));
+  const int d = grid->dim;
+  if (d != 2 && d != 3) return bail(fail(h, JFFT_ERR_ARG, "dim must be 2 or 3"));
+  const int nmax = d == 2 ? 2048 : 1024;
+  Grid& g = h->g;
+  g.d = d;
+  g.N = 1;
+  for (int a = 0; a < d; ++a) {
+    const int64_t n = grid->n[a];
+    if (!is_pow2(n) || n < 4) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "each n must be a power of two >= 4"));
+    if (n > nmax) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "grid exceeds the largest supported axis length"));
+    g.n[a] = (int)n;
+    g.log2n[a] = ilog2i(n);
+    g.N *= n;
+  }
+  g.M = g.n[d - 1] / 2;
+  g.F = g.N / g.n[d - 1] * (g.M + 1);
+  h->ds = d * (d + 1) / 2;
+  if (o.precision != JFFT_PREC_FP64) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "only FP64 precision is built"));
+  if (o.max_iter <= 0) return bail(fail(h, JFFT_ERR_ARG, "max_iter must be positive"));
+  if (o.stop_mode != JFFT_STOP_REL && o.stop_mode != JFFT_STOP_ABS_SQ) return bail(fail(h, JFFT_ERR_ARG, "bad stop_mode"));
+  if (o.check_every <= 0) o.check_every = 8;
+  if (o.max_loads <= 0) o.max_loads = 6;
+  if (o.max_loads < d) o.max_loads = d;
+  if (o.max_loads > kMaxLoads) return bail(fail(h, JFFT_ERR_ARG, "max_loads too large"));
+  if (!(o.void_value > 0.0 && std::isfinite(o.void_value))) return bail(fail(h, JFFT_ERR_ARG, "void_value must be > 0"));
+  if (o.io_memory != JFFT_MEM_HOST && o.io_memory != JFFT_MEM_DEVICE) return bail(fail(h, JFFT_ERR_ARG, "bad io_memory"));
+  h->opt = o;
+  h->io = o.io_memory;
+  h->max_iter = o.max_iter;
+  h->max_loads = o.max_loads;
+  h->device = o.device;
+  if (!mat) return bail(fail(h, JFFT_ERR_ARG, "material is NULL"));
+  h->nu = mat->nu;
+  jfft_status s = validate_material(h, mat, g.N);
+  if (s) return bail(s);
+
+  // unit material and reference material
+  const double lam_u = mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
+  const double mu_u = 1.0 / (2.0 * (1.0 + mat->nu));
+  double hh[3];
+  for (int a = 0; a < d; ++a) hh[a] = 1.0 / g.n[a];
+  h->ec = make_elem_const(d, hh, lam_u, mu_u);
+  if (C_ref) {
+    const int ds = h->ds;
+    const double lam = C_ref[1], mu = 0.5 * (C_ref[0] - C_ref[1]);
+    double want[36];
+    isotropic_mandel(d, lam, mu, want);
+    double scale = 0.0;
+    for (int i = 0; i < ds * ds; ++i) scale = std::max(scale, std::fabs(want[i]));
+    for (int i = 0; i < ds * ds; ++i)
+      if (!(std::fabs(C_ref[i] - want[i]) <= 1e-12 * scale))
+        return bail(fail(h, JFFT_ERR_UNSUPPORTED, "C_ref must be an isotropic Mandel matrix"));
+    if (!(mu > 0.0) || !(lam + 2.0 * mu / d > 0.0))
+      return bail(fail(h, JFFT_ERR_ARG, "C_ref must be positive definite"));
+    h->cref_mean = false;
+    h->cref_lam = lam;
+    h->cref_mu = mu;
+  }
+  // kappa_a: diagonal of the unit element matrix (corner independent)
+  for (int a = 0; a < 3; ++a) h->kappa[a] = 1.0;
+  for (int a = 0; a < d; ++a) {
+    if (d == 2) {
+      double u[2][4] = {};
+      u[a][0] = 1.0;
+      element_force<2, double, false>(h->ec, nullptr, u, 1.0);
+      h->kappa[a] = u[a][0];
+    } else {
+      double u[3][8] = {};
+      u[a][0] = 1.0;
+      element_force<3, double, false>(h->ec, nullptr, u, 1.0);
+      h->kappa[a] = u[a][0];
+    }
+    h->jscale[a] = 1.0 / std::sqrt(h->kappa[a]);
+  }
+  h->void_js = 1.0 / std::sqrt(o.void_value);
+  h->scale_store = 1.0 / (2.0 * (double)g.N);
+
+  cudaError_t ce = cudaSetDevice(h->device);
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaSetDevice"));
+  h->st = (cudaStream_t)o.stream;
+  g_cur = h;
+
+  // workspace plan
+  const int64_t fe = field_elems(h);
+  const int nbmax = h->max_loads;
+  const int64_t spec_n = (int64_t)nbmax * d * g.F;
+  size_t total = 0;
+  total += 4 * g.N * sizeof(double);                               // field, E, esum, js
+  total += (size_t)g.F * h->ds * sizeof(double);                    // G
+  for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(double2);
+  total += (size_t)spec_n * sizeof(double2) * (d == 3 ? 2 : 1);     // T (U)
+  total += 5 * (size_t)nbmax * fe * sizeof(double);                 // x r p q z
+  const size_t part_rows = (size_t)nbmax * 6;
+  total += part_rows * kMaxPartials * sizeof(double);
+  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift));
+  if (o.hbm_budget && total > o.hbm_budget) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds hbm_budget %zu", total, o.hbm_budget);
+    return bail(fail(h, JFFT_ERR_OOM, msg));
+  }
+  size_t fr = 0, tot = 0;
+  ce = cudaMemGetInfo(&fr, &tot);
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMemGetInfo"));
+  if (total > fr) return bail(fail(h, JFFT_ERR_OOM, "workspace does not fit the free device memory"));
+
+#define AL(ptr, bytes) do { jfft_status s_ = dalloc(h, (void**)&(ptr), (bytes)); if (s_) return bail(s_); } while (0)
+  AL(h->field, g.N * sizeof(double));
+  AL(h->E, g.N * sizeof(double));
+  AL(h->esum, g.N * sizeof(double));
+  AL(h->js, g.N * sizeof(double));
+  AL(h->G, (size_t)g.F * h->ds * sizeof(double));
+  for (int a = 0; a < d; ++a) AL(h->tw[a], (size_t)g.n[a] * sizeof(double2));
+  AL(h->T, (size_t)spec_n * sizeof(double2));
+  if (d == 3) AL(h->U, (size_t)spec_n * sizeof(double2));
+  AL(h->x, (size_t)nbmax * fe * sizeof(double));
+  AL(h->r, (size_t)nbmax * fe * sizeof(double));
+  AL(h->p, (size_t)nbmax * fe * sizeof(double));
+  AL(h->q, (size_t)nbmax * fe * sizeof(double));
+  AL(h->z, (size_t)nbmax * fe * sizeof(double));
+  AL(h->partial, part_rows * kMaxPartials * sizeof(double));
+  AL(h->red, 1024 * sizeof(double));
+  AL(h->cg, nbmax * sizeof(CgState));
+  AL(h->shifts, nbmax * sizeof(StrainShift));
+#undef AL
+  ce = cudaMallocHost((void**)&h->cg_h, nbmax * sizeof(CgState));
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
+  ce = cudaMallocHost((void**)&h->red_h, 1024 * sizeof(double));
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
+
+  for (int a = 0; a < d; ++a) {
+    ce = launch_twiddles(h->tw[a], g.n[a], h->st);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "twiddles"));
+  }
+  s = setup_material(h, mat, false);
+  if (s) return bail(s);
+  g_cur = nullptr;
+  *out = h;
+  return JFFT_OK;
+}
+
+extern "C" void jfft_destroy(jfft_solver* h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+extern "C" jfft_status jfft_set_material(jfft_solver* h, const jfft_material* m) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  return setup_material(h, m, h->io == JFFT_MEM_DEVICE);
+}
+
+extern "C" const char* jfft_status_string(jfft_status s) {
+  switch (s) {
+    case JFFT_OK: return "ok";
+    case JFFT_ERR_ARG: return "invalid argument";
+    case JFFT_ERR_OOM: return "out of device memory or over budget";
+    case JFFT_ERR_CUDA: return "CUDA error";
+    case JFFT_ERR_NOCONV: return "not converged within max_iter";
+    case JFFT_ERR_BREAKDOWN: return "CG breakdown";
+    case JFFT_ERR_TIMEOUT: return "device wait timed out";
+    case JFFT_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* jfft_last_error(const jfft_solver* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+extern "C" jfft_status jfft_set_io_memory(jfft_solver* h, int io) {
+  if (!h) return JFFT_ERR_ARG;
+  if (io != JFFT_MEM_HOST && io != JFFT_MEM_DEVICE) return fail(h, JFFT_ERR_ARG, "bad io memory");
+  h->io = io;
+  return JFFT_OK;
+}
+
+extern "C" jfft_status jfft_set_max_iter(jfft_solver* h, int max_iter) {
+  if (!h) return JFFT_ERR_ARG;
+  if (max_iter <= 0) return fail(h, JFFT_ERR_ARG, "max_iter must be positive");
+  h->max_iter = max_iter;
+  return JFFT_OK;
+}
+
+// ------------------------------------------------------------- PCG driver
+static bool valid_pc(int pc) {
+  return pc == JFFT_PC_NONE || pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI || pc == JFFT_PC_JACOBI;
+}
+
+static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, int nb, const CgState* cg, int* np) {
+  const Grid& g = h->g;
+  if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI) {
+    FftPlan pl = {{h->tw[0], h->tw[1], h->tw[2]}, h->T, h->U, h->G};
+    CK(launch_green_precond(g, pl, r, z, nb, field_elems(h), h->js, h->jscale, h->void_js,
+                            pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st));
+  } else {
+    CK(launch_jacobi_precond(g, r, z, nb, field_elems(h), h->js, h->jscale, h->void_js, pc == JFFT_PC_NONE, h->partial,
+                             np, cg, h->st));
+  }
+  return JFFT_OK;
+}
+
+// Runs PCG on r (holding f) with x = 0 for nb right-hand sides. INIT_FF must have run.
+static jfft_status pcg_core(jfft_solver* h, int nb, int pc, double tol, int* status_out) {
+  const Grid& g = h->g;
+  const int64_t fe = field_elems(h);
+  int np = 0;
+  jfft_status s;
+  CK(launch_fill(h->x, nb * fe, 0.0, h->st));
+  CK(launch_fill(h->p, nb * fe, 0.0, h->st));
+  s = precond(h, pc, h->r, h->z, nb, h->cg, &np);
+  if (s) return s;
+  CK(launch_cg_scalars(kStageInitGamma, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
+  CK(launch_cg_p(g, h->p, h->z, nb, fe, h->cg, h->st));
+  const int chunk = h->opt.check_every;
+  int64_t launched = 0;
+  const int64_t cap = (int64_t)h->max_iter + chunk;
+  while (true) {
+    for (int c = 0; c < chunk; ++c) {
+      CK(launch_apply_K(g, h->ec, h->E, 0.0, h->p, h->q, nb, fe, nullptr, 1.0, 1, h->partial, &np, h->cg, h->st));
+      CK(launch_cg_scalars(kStageAlpha, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
+      CK(launch_cg_xr(g, h->x, h->r, h->p, h->q, nb, fe, h->cg, h->partial, &np, h->st));
+      CK(launch_cg_scalars(kStageRR, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
+      s = precond(h, pc, h->r, h->z, nb, h->cg, &np);
+      if (s) return s;
+      CK(launch_cg_scalars(kStageBeta, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
+      CK(launch_cg_p(g, h->p, h->z, nb, fe, h->cg, h->st));
+    }
+    launched += chunk;
+    CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
+    s = sync(h);
+    if (s) return s;
+    bool all = true;
+    for (int b = 0; b < nb; ++b) all = all && h->cg_h[b].done != kRunning;
+    if (all) break;
+    if (launched > cap) return fail(h, JFFT_ERR_CUDA, "PCG driver exceeded its iteration cap");
+  }
+  int worst = kConverged;
+  for (int b = 0; b < nb; ++b) {
+    const int dn = h->cg_h[b].done;
+    if (dn == kBreakdown) worst = kBreakdown;
+    else if (dn == kNoConv && worst != kBreakdown) worst = kNoConv;
+  }
+  *status_out = worst;
+  return JFFT_OK;
+}
+
+static jfft_status upload_shifts(jfft_solver* h, int n, const double* eps) {
+  std::vector<StrainShift> sh(n);
+  for (int b = 0; b < n; ++b) {
+    for (int c = 0; c < h->ds; ++c)
+      if (!std::isfinite(eps[b * h->ds + c])) return fail(h, JFFT_ERR_ARG, "macroscopic strain must be finite");
+    sh[b] = make_shift(h->g.d, h->ec, eps + b * h->ds);
+  }
+  CK(cudaMemcpyAsync(h->shifts, sh.data(), n * sizeof(StrainShift), cudaMemcpyHostToDevice, h->st));
+  // the pageable source must stay alive until the copy has been staged
+  CK(cudaStreamSynchronize(h->st));
+  return JFFT_OK;
+}
+
+static jfft_status check_count(jfft_solver* h, int count) {
+  if (count <= 0 || count > h->max_loads) return fail(h, JFFT_ERR_ARG, "count must be in [1, max_loads]");
+  return JFFT_OK;
+}
+
+extern "C" jfft_status jfft_solve(jfft_solver* h, int n_loads, const double* eps_bar, double tol, int pc,
+                                  jfft_result* res) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = check_count(h, n_loads);
+  if (s) return s;
+  if (!eps_bar) return fail(h, JFFT_ERR_ARG, "eps_bar is NULL");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, JFFT_ERR_ARG, "tol must be finite and >= 0");
+  if (!valid_pc(pc)) return fail(h, JFFT_ERR_ARG, "unknown preconditioner");
+  if (h->io == JFFT_MEM_DEVICE) {
+    std::vector<double> eh(n_loads * h->ds);
+    CK(cudaMemcpy(eh.data(), eps_bar, eh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    s = upload_shifts(h, n_loads, eh.data());
+  } else {
+    s = upload_shifts(h, n_loads, eps_bar);
+  }
+  if (s) return s;
+  const Grid& g = h->g;
+  const int64_t fe = field_elems(h);
+  const int nb = n_loads;
+  int np = 0;
+  // S2: r = f = -B^T W C eps_bar, ||f||^2
+  CK(launch_apply_K(g, h->ec, h->E, 0.0, nullptr, h->r, nb, fe, h->shifts, -1.0, 2, h->partial, &np, nullptr, h->st));
+  CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
+  int st = kConverged;
+  s = pcg_core(h, nb, pc, tol, &st);
+  if (s) return s;
+  // S8: zero-mean fluctuation
+  CK(launch_row_sums(h->x, nb * g.d, g.N, h->partial, &np, h->st));
+  CK(launch_reduce_partials(h->partial, np, nb * g.d, kMaxPartials, h->red, h->st));
+  CK(launch_sub_mean(h->x, nb * g.d, g.N, h->red, h->st));
+  // true residual f - K u = -B^T W C (eps_bar + B u)
+  CK(launch_apply_K(g, h->ec, h->E, 0.0, h->x, h->q, nb, fe, h->shifts, -1.0, 2, h->partial, &np, nullptr, h->st));
+  CK(launch_reduce_partials(h->partial, np, nb, kMaxPartials, h->red, h->st));
+  // stresses and homogenised stiffness
+  double* stress_dev = (res && res->stress) ? h->z : nullptr;
+  if (stress_dev && (int64_t)h->ds * g.N * nb > (int64_t)h->max_loads * fe) stress_dev = nullptr;
+  CK(launch_stress(g, h->ec, h->E, h->x, nb, h->shifts, stress_dev, h->partial, &np, h->st));
+  CK(launch_reduce_partials(h->partial, np, nb * h->ds, kMaxPartials, h->red + nb, h->st));
+  CK(cudaMemcpyAsync(h->red_h, h->red, nb * (1 + h->ds) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
+  s = sync(h);
+  if (s) return s;
+  if (res) {
+    if (res->u) { s = copy_out(h, res->u, h->x, nb * fe * sizeof(double)); if (s) return s; }
+    if (res->stress) {
+      if (stress_dev) {
+        s = copy_out(h, res->stress, stress_dev, (size_t)nb * h->ds * g.N * sizeof(double));
+      } else {
+        // stress of many loads: one load at a time through the z buffer
+        for (int b = 0; b < nb && !s; ++b) {
+          CK(launch_stress(g, h->ec, h->E, h->x + b * fe, 1, h->shifts + b, h->z, h->partial, &np, h->st));
+          s = copy_out(h, res->stress + (size_t)b * h->ds * g.N, h->z, (size_t)h->ds * g.N * sizeof(double));
+        }
+      }
+      if (s) return s;
+    }
+    std::vector<double> chom(h->ds * nb), rel(nb);
+    std::vector<int> its(nb);
+    for (int b = 0; b < nb; ++b) {
+      const double ff = h->cg_h[b].ff;
+      rel[b] = ff > 0.0 ? std::sqrt(h->red_h[b] / ff) : 0.0;
+      its[b] = h->cg_h[b].iters;
+      for (int c = 0; c < h->ds; ++c) chom[c * nb + b] = h->red_h[nb + b * h->ds + c];
+    }
+    if (h->io == JFFT_MEM_DEVICE) {
+      if (res->C_hom) CK(cudaMemcpy(res->C_hom, chom.data(), chom.size() * sizeof(double), cudaMemcpyHostToDevice));
+      if (res->rel_res) CK(cudaMemcpy(res->rel_res, rel.data(), nb * sizeof(double), cudaMemcpyHostToDevice));
+      if (res->iters) CK(cudaMemcpy(res->iters, its.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+    } else {
+      if (res->C_hom) std::memcpy(res->C_hom, chom.data(), chom.size() * sizeof(double));
+      if (res->rel_res) std::memcpy(res->rel_res, rel.data(), nb * sizeof(double));
+      if (res->iters) std::memcpy(res->iters, its.data(), nb * sizeof(int));
+    }
+  }
+  s = sync(h);
+  if (s) return s;
+  if (st == kBreakdown) return fail(h, JFFT_ERR_BREAKDOWN, "CG breakdown (non-positive or non-finite p.Kp or r.z)");
+  if (st == kNoConv) return fail(h, JFFT_ERR_NOCONV, "max_iter reached before the stopping rule held");
+  return JFFT_OK;
+}
+
+// ------------------------------------------------------------- building blocks
+extern "C" jfft_status jfft_get_material(jfft_solver* h, double* E) {
+  if (!h || !E) return h ? fail(h, JFFT_ERR_ARG, "NULL output") : JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = copy_out(h, E, h->E, h->g.N * sizeof(double));
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_rhs(jfft_solver* h, int count, const double* eps, double* f) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = check_count(h, count);
+  if (s) return s;
+  if (!eps || !f) return fail(h, JFFT_ERR_ARG, "NULL argument");
+  std::vector<double> eh(count * h->ds);
+  if (h->io == JFFT_MEM_DEVICE) CK(cudaMemcpy(eh.data(), eps, eh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  else std::memcpy(eh.data(), eps, eh.size() * sizeof(double));
+  s = upload_shifts(h, count, eh.data());
+  if (s) return s;
+  CK(launch_apply_K(h->g, h->ec, h->E, 0.0, nullptr, h->r, count, field_elems(h), h->shifts, -1.0, 0, nullptr, nullptr,
+                    nullptr, h->st));
+  s = copy_out(h, f, h->r, count * field_elems(h) * sizeof(double));
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_apply_K(jfft_solver* h, int count, const double* x, double* y) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = check_count(h, count);
+  if (s) return s;
+  if (!x || !y) return fail(h, JFFT_ERR_ARG, "NULL argument");
+  const int64_t fe = field_elems(h);
+  s = copy_in(h, h->p, x, count * fe);
+  if (s) return s;
+  CK(launch_apply_K(h->g, h->ec, h->E, 0.0, h->p, h->q, count, fe, nullptr, 1.0, 0, nullptr, nullptr, nullptr, h->st));
+  s = copy_out(h, y, h->q, count * fe * sizeof(double));
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_get_diag(jfft_solver* h, int method, double* diag) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  if (!diag) return fail(h, JFFT_ERR_ARG, "NULL output");
+  const Grid& g = h->g;
+  if (method == JFFT_DIAG_CLOSED_FORM) {
+    CK(launch_diag_closed(g, h->esum, h->kappa, h->z, h->st));
+  } else if (method == JFFT_DIAG_COMBS) {
+    for (int a = 0; a < g.d; ++a)
+      for (int off = 0; off < (1 << g.d); ++off) {
+        CK(launch_fill_comb(g, a, off, h->p, h->st));
+        CK(launch_apply_K(g, h->ec, h->E, 0.0, h->p, h->q, 1, field_elems(h), nullptr, 1.0, 0, nullptr, nullptr,
+                          nullptr, h->st));
+        CK(launch_extract_comb(g, a, off, h->q, h->z, h->st));
+      }
+  } else {
+    return fail(h, JFFT_ERR_ARG, "unknown diagonal method");
+  }
+  jfft_status s = copy_out(h, diag, h->z, field_elems(h) * sizeof(double));
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_get_green(jfft_solver* h, double* G) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  if (!G) return fail(h, JFFT_ERR_ARG, "NULL output");
+  const Grid& g = h->g;
+  CK(launch_green_export(g, h->G, h->z, h->scale_store, h->st));
+  jfft_status s = copy_out(h, G, h->z, (size_t)g.F * g.d * g.d * sizeof(double));
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_apply_precond(jfft_solver* h, int pc, int count, const double* r, double* z) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = check_count(h, count);
+  if (s) return s;
+  if (!valid_pc(pc)) return fail(h, JFFT_ERR_ARG, "unknown preconditioner");
+  if (!r || !z) return fail(h, JFFT_ERR_ARG, "NULL argument");
+  const int64_t fe = field_elems(h);
+  s = copy_in(h, h->r, r, count * fe);
+  if (s) return s;
+  int np = 0;
+  s = precond(h, pc, h->r, h->z, count, nullptr, &np);
+  if (s) return s;
+  s = copy_out(h, z, h->z, count * fe * sizeof(double));
+  if (s) return s;
+  return sync(h);
+}
+
+extern "C" jfft_status jfft_solve_rhs(jfft_solver* h, int count, const double* f, double tol, int pc, double* u,
+                                      int* iters) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = check_count(h, count);
+  if (s) return s;
+  if (!f) return fail(h, JFFT_ERR_ARG, "f is NULL");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, JFFT_ERR_ARG, "tol must be finite and >= 0");
+  if (!valid_pc(pc)) return fail(h, JFFT_ERR_ARG, "unknown preconditioner");
+  const int64_t fe = field_elems(h);
+  s = copy_in(h, h->r, f, count * fe);
+  if (s) return s;
+  int np = 0;
+  CK(launch_dot(h->g, h->r, h->r, count, fe, h->partial, &np, h->st));
+  CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, count, tol, h->opt.stop_mode, h->max_iter, h->st));
+  int st = kConverged;
+  s = pcg_core(h, count, pc, tol, &st);
+  if (s) return s;
+  if (u) { s = copy_out(h, u, h->x, count * fe * sizeof(double)); if (s) return s; }
+  if (iters) {
+    std::vector<int> its(count);
+    for (int b = 0; b < count; ++b) its[b] = h->cg_h[b].iters;
+    if (h->io == JFFT_MEM_DEVICE) CK(cudaMemcpy(iters, its.data(), count * sizeof(int), cudaMemcpyHostToDevice));
+    else std::memcpy(iters, its.data(), count * sizeof(int));
+  }
+  s = sync(h);
+  if (s) return s;
+  if (st == kBreakdown) return fail(h, JFFT_ERR_BREAKDOWN, "CG breakdown");
+  if (st == kNoConv && tol > 0.0) return fail(h, JFFT_ERR_NOCONV, "max_iter reached before the stopping rule held");
+  return JFFT_OK;
+}
+
+extern "C" jfft_status jfft_postprocess(jfft_solver* h, int count, const double* eps, const double* u, double* stress,
+                                        double* C_hom) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = check_count(h, count);
+  if (s) return s;
+  if (!eps || !u) return fail(h, JFFT_ERR_ARG, "NULL argument");
+  const Grid& g = h->g;
+  const int64_t fe = field_elems(h);
+  std::vector<double> eh(count * h->ds);
+  if (h->io == JFFT_MEM_DEVICE) CK(cudaMemcpy(eh.data(), eps, eh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  else std::memcpy(eh.data(), eps, eh.size() * sizeof(double));
+  s = upload_shifts(h, count, eh.data());
+  if (s) return s;
+  s = copy_in(h, h->x, u, count * fe);
+  if (s) return s;
+  std::vector<double> chom(h->ds * count);
+  for (int b = 0; b < count; ++b) {
+    int np = 0;
+    CK(launch_stress(g, h->ec, h->E, h->x + b * fe, 1, h->shifts + b, stress ? h->z : nullptr, h->partial, &np, h->st));
+    CK(launch_reduce_partials(h->partial, np, h->ds, kMaxPartials, h->red, h->st));
+    CK(cudaMemcpyAsync(h->red_h, h->red, h->ds * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    if (stress) { s = copy_out(h, stress + (size_t)b * h->ds * g.N, h->z, (size_t)h->ds * g.N * sizeof(double)); if (s) return s; }
+    s = sync(h);
+    if (s) return s;
+    for (int c = 0; c < h->ds; ++c) chom[c * count + b] = h->red_h[c];
+  }
+  if (C_hom) {
+    if (h->io == JFFT_MEM_DEVICE) CK(cudaMemcpy(C_hom, chom.data(), chom.size() * sizeof(double), cudaMemcpyHostToDevice));
+    else std::memcpy(C_hom, chom.data(), chom.size() * sizeof(double));
+  }
+  return JFFT_OK;
+}
+
+// ------------------------------------------------------------- instrumentation
+extern "C" int64_t jfft_launch_count(const jfft_solver* h) { return h ? h->launches : 0; }
+
+extern "C" jfft_status jfft_set_profiling(jfft_solver* h, int on) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  jfft_status s = sync(h);
+  if (s) return s;
+  h->profiling = on != 0;
+  if (on) h->prof.clear();
+  return JFFT_OK;
+}
+
+extern "C" const char* jfft_profile_json(jfft_solver* h) {
+  if (!h) return "{}";
+  {
+    CurGuard guard(h);
+    if (sync(h)) return "{}";
+  }
+  std::string s = "{";
+  bool first = true;
+  for (auto& kv : h->prof) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s\"%s\": [%lld, %.6f]", first ? "" : ", ", kv.first.c_str(), (long long)kv.second.first,
+             kv.second.second);
+    s += buf;
+    first = false;
+  }
+  s += "}";
+  h->prof_json = s;
+  return h->prof_json.c_str();
+}
+
+extern "C" size_t jfft_workspace_bytes(const jfft_solver* h) { return h ? h->ws_bytes : 0; }

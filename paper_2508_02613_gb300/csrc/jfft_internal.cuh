@@ -1,0 +1,164 @@
+// Internal declarations of the J-FFT CUDA library: device helpers, element
+// constants and the kernel launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace jfft {
+
+// ---------------------------------------------------------------- basics
+template <typename T> struct c2;
+template <> struct c2<double> { using t = double2; };
+template <> struct c2<float> { using t = float2; };
+template <typename T> using cplx = typename c2<T>::t;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T x, T y) { cplx<T> r; r.x = x; r.y = y; return r; }
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxLoads = 64;
+
+// Launch geometry of one grid, shared by every kernel.
+struct Grid {
+  int d;            // 2 or 3
+  int n[3];         // nodal points per axis (n[d-1] is the contiguous axis)
+  int log2n[3];
+  int64_t N;        // product of n
+  int M;            // n[d-1] / 2, half length of the real axis
+  int64_t F;        // number of half-spectrum frequencies: N / n[d-1] * (M + 1)
+};
+
+// Element constants of the Q1 operator in Walsh-Hadamard mode form.
+//
+// Per element, each displacement component X_a is expanded in the 2^d corner
+// modes W_a[m] = sum_o prod_{b in m} (2 o_b - 1) u_a(o) (m a bit set over axes,
+// axis 0 = highest bit). With the full 2^d Gauss rule, distinct monomials of the
+// local coordinates are orthogonal, so the element energy splits by monomial mu
+// (a set of axes, |mu| < d) with weight vol * 3^-|mu|. The mode forces are linear
+// in the modes; the tables below hold those coefficients for unit E:
+//   normal  F_a[mu+a] += nrm[k][a][b] W_b[mu+b]           (a, b not in mu)
+//   shear   F_a[mu+b] += shr[k][b][b] W_a[mu+b] + shr[k][a][b] W_b[mu+a]  (a != b not in mu)
+//   locked  F_c[mu+a] += shr[k][a][a] W_c[mu+a]            (a not in mu, c in mu)
+// with k = |mu|, gs_a = (2 / h_a) / 2^d, kappa_k = vol 3^-k,
+//   nrm[k][a][b] = (a == b ? lambda + 2 mu : lambda) kappa_k gs_a gs_b,
+//   shr[k][a][b] = mu kappa_k gs_a gs_b.
+// Nodal forces are the inverse transform of F times E_e.
+struct ElemConst {
+  double nrm[3][3][3];
+  double shr[3][3][3];
+  double gs[3];       // (2 / h_a) / 2^d: mode -> displacement-gradient factor
+  double lam, mu;     // Lame constants of the unit material
+  double vol;         // element volume
+};
+
+// Macroscopic strain of one load case expressed as a shift of the single-axis
+// modes: W_a[{b}] += shift[a][b] turns B u into eps_bar + B u at every Gauss point.
+struct StrainShift {
+  double s[kMaxDim][kMaxDim];
+};
+
+// PCG scalars of one right-hand side, resident on the device.
+struct CgState {
+  double gamma;     // r . z
+  double alpha, beta;
+  double rr;        // ||r||^2
+  double ff;        // ||f||^2
+  double rr_stop;   // threshold on rr
+  int iters;
+  int done;         // 0 running, 1 converged, 2 max_iter reached, 3 breakdown
+  int max_iter;
+  int pad;
+};
+
+enum CgDone { kRunning = 0, kConverged = 1, kNoConv = 2, kBreakdown = 3 };
+
+// Reduction buffers: partial sums per (row, block), reduced in a fixed order.
+constexpr int kMaxPartials = 1 << 17;
+
+// Every kernel launch is bracketed by these hooks (launch counting and optional
+// CUDA-event timing per kernel name); implemented by the API layer.
+void hook_begin(const char* name, cudaStream_t st);
+void hook_end(const char* name, cudaStream_t st);
+#define JFFT_K(name, st, ...) \
+  do { ::jfft::hook_begin(name, st); __VA_ARGS__; ::jfft::hook_end(name, st); } while (0)
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return cudaGetLastError(). `nparts` receives
+// the number of partial sums written per row.
+
+// S1: E[i] = e_min + (e_max - e_min) field[i]^expo (kind 1) or E = field (kind 0).
+cudaError_t launch_material(const double* field, double* E, int64_t N, int kind, double e_min, double e_max,
+                            double expo, cudaStream_t st);
+
+// bad += number of entries of f that are negative or not finite.
+cudaError_t launch_check_field(const double* f, int64_t N, int* bad, cudaStream_t st);
+
+// S2 / S3: y_b = sgn * B^T W C_e (shift_b + B x_b) for b in [0, nb). x == NULL: pure
+// macro-strain load; E == NULL: uniform modulus e_uniform; shifts == NULL: no shift.
+// dot_mode 1: partial[b][blk] = sum x.y ; 2: sum y.y ; 0: none. Rhs b is skipped
+// when cg != NULL and cg[b].done.
+cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
+                           double* y, int nb, int64_t field_stride, const StrainShift* shifts, double sgn, int dot_mode,
+                           double* partial, int* nparts, const CgState* cg, cudaStream_t st);
+
+// S8: element-averaged Mandel stress [nb][d*][N] (stress may be NULL) and partial
+// sums of vol * stress in partial[(b d* + s) * kMaxPartials + blk].
+cudaError_t launch_stress(const Grid& g, const ElemConst& ec, const double* E, const double* u, int nb,
+                          const StrainShift* shifts, double* stress, double* partial, int* nparts, cudaStream_t st);
+
+// S5: esum[I] = sum of E over the 2^d voxels at node I; js = esum^-1/2 (0 for 0).
+cudaError_t launch_node_esum(const Grid& g, const double* E, double* esum, cudaStream_t st);
+cudaError_t launch_jacobi_half(const double* esum, double* js, int64_t N, cudaStream_t st);
+// diag[a][I] = kappa[a] * esum[I]
+cudaError_t launch_diag_closed(const Grid& g, const double* esum, const double* kappa3, double* diag, cudaStream_t st);
+// Alg. 2 helpers: comb field of one component / offset pattern, and extraction.
+cudaError_t launch_fill_comb(const Grid& g, int comp, int offbits, double* x, cudaStream_t st);
+cudaError_t launch_extract_comb(const Grid& g, int comp, int offbits, const double* y, double* diag, cudaStream_t st);
+// S9 (Alg. 1): d unit-impulse fields [d][d][N]; block inversion into the table.
+cudaError_t launch_impulses(const Grid& g, double* x, cudaStream_t st);
+cudaError_t launch_green_table(const Grid& g, const double2* spec, double* G, double scale_store, cudaStream_t st);
+cudaError_t launch_green_export(const Grid& g, const double* G, double* out, double scale_store, cudaStream_t st);
+
+// S6: twiddle table exp(-2 pi i m / n), m < n.
+cudaError_t launch_twiddles(double2* tw, int n, cudaStream_t st);
+
+struct FftPlan {
+  const double2* tw[3];
+  double2* T;        // spectrum buffer (real-axis pass output)
+  double2* U;        // second spectrum buffer (3D)
+  const double* G;   // stored symbol table [F][d*]
+};
+
+// S5 + S6: z_b = M^-1 r_b (Green, or Green-Jacobi when jacobi), with the partial
+// sums of r.z. jscale[a] = kappa_a^-1/2; void nodes use void_js.
+cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
+                                 int64_t field_stride, const double* js, const double* jscale, double void_js,
+                                 bool jacobi, double* partial, int* nparts, const CgState* cg, cudaStream_t st);
+// Forward transform of nb d-component real fields -> line-major spectrum [nb][d][F].
+cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
+                                    const double2** spec_out, cudaStream_t st);
+// z = J r (J = diag(K)^-1 with the void rule) or z = r (identity), partial r.z.
+cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
+                                  const double* jscale, double void_js, bool identity, double* partial, int* nparts,
+                                  const CgState* cg, cudaStream_t st);
+
+// S4: CG vector updates and inner products.
+cudaError_t launch_cg_xr(const Grid& g, double* x, double* r, const double* p, const double* q, int nb, int64_t stride,
+                         CgState* cg, double* partial, int* nparts, cudaStream_t st);
+cudaError_t launch_cg_p(const Grid& g, double* p, const double* z, int nb, int64_t stride, CgState* cg, cudaStream_t st);
+cudaError_t launch_dot(const Grid& g, const double* a, const double* c, int nb, int64_t stride, double* partial,
+                       int* nparts, cudaStream_t st);
+// S4 / S7: scalar stages, one block per rhs.
+enum ScalarStage { kStageInitFF = 0, kStageInitGamma = 1, kStageAlpha = 2, kStageRR = 3, kStageBeta = 4 };
+cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,
+                              int stop_mode, int max_iter, cudaStream_t st);
+// out[row] = sum_j partial[row * pstride + j] in a fixed order.
+cudaError_t launch_reduce_partials(const double* partial, int nparts, int rows, int64_t pstride, double* out,
+                                   cudaStream_t st);
+// Row sums of x viewed as [rows][n] into partials; x[row][:] -= sums[row] / n.
+cudaError_t launch_row_sums(const double* x, int rows, int64_t n, double* partial, int* nparts, cudaStream_t st);
+cudaError_t launch_sub_mean(double* x, int rows, int64_t n, const double* sums, cudaStream_t st);
+cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t st);
+
+}  // namespace jfft

@@ -1,0 +1,488 @@
+// Operator-side kernels of the J-FFT solver: material (S1), matrix-free stiffness
+// K = B^T W C B and the macro-strain load (S2, S3; paper Sec. 3.1 "Matrix-free
+// assembly", Eq. lin_system_exp), element stress (S8), the Jacobi diagonal and
+// Alg. 2 combs (S5), and the Alg. 1 impulse / inversion steps (S9).
+#include "element.cuh"
+#include "reduce.cuh"
+
+namespace jfft {
+
+// ------------------------------------------------------------------ S1
+__global__ void k_material(const double* __restrict__ field, double* __restrict__ E, int64_t N, int kind,
+                           double e_min, double e_max, double expo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = field[i];
+    E[i] = kind == 1 ? e_min + (e_max - e_min) * pow(v, expo) : v;
+  }
+}
+
+// Counts entries that are negative or not finite (device-side validation of a
+// material field given in device memory).
+__global__ void k_check_field(const double* __restrict__ f, int64_t N, int* __restrict__ bad) {
+  int local = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = f[i];
+    local += (!isfinite(v) || v < 0.0) ? 1 : 0;
+  }
+  if (local) atomicAdd(bad, local);
+}
+
+cudaError_t launch_check_field(const double* f, int64_t N, int* bad, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 8);
+  JFFT_K("check_field", st, k_check_field<<<blocks, 256, 0, st>>>(f, N, bad));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_material(const double* field, double* E, int64_t N, int kind, double e_min, double e_max,
+                            double expo, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
+  JFFT_K("material", st, k_material<<<blocks, 256, 0, st>>>(field, E, N, kind, e_min, e_max, expo));
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ S3 / S2
+// Marching tile. The CTA owns an in-plane tile of P1 x P2 nodes (axes 1..d-1; P2 = 1
+// in 2D) and walks `seg` node layers along axis 0. For element layer e0 it needs
+// node layers e0 and e0 + 1 (a two-slot ring in shared memory, with a one-node halo
+// on the low in-plane side and the high side), computes the (P1+1) x (P2+1) elements
+// of the layer once each, scatters their corner forces through shared memory, and
+// completes node layer e0 from the o0 = 0 corners plus the o0 = 1 corners of layer
+// e0 - 1 carried in registers.
+struct MarchGeom {
+  int P1, P2;        // in-plane node tile (P2 = 1 in 2D)
+  int seg;           // node layers per CTA
+  int tiles1, tiles2;
+};
+
+template <int D> __host__ __device__ inline int plane_nodes(const MarchGeom& m) { return (m.P1 + 2) * (D == 3 ? m.P2 + 2 : 1); }
+template <int D> __host__ __device__ inline int plane_elems(const MarchGeom& m) { return (m.P1 + 1) * (D == 3 ? m.P2 + 1 : 1); }
+
+template <int D> static size_t march_smem(const MarchGeom& m) {
+  const int pn = plane_nodes<D>(m), pe = plane_elems<D>(m);
+  return sizeof(double) * (size_t(2) * D * pn + pe + size_t(D) * (1 << D) * pe);
+}
+
+// DOT: 0 none, 1 sum x.y, 2 sum y.y
+template <int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
+__global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst ec, const double* __restrict__ E,
+                                                 double e_uniform, const double* __restrict__ x, double* __restrict__ y,
+                                                 int64_t fstride, const StrainShift* __restrict__ shifts, double sgn,
+                                                 double* __restrict__ partial, const CgState* __restrict__ cg) {
+  constexpr int NC = 1 << D;
+  constexpr int NCP = NC / 2;  // in-plane corners
+  const int b = blockIdx.z;
+  if (cg && cg[b].done) return;
+  extern __shared__ double sm[];
+  const int pn = plane_nodes<D>(mg), pe = plane_elems<D>(mg);
+  double* ring = sm;                       // [2][D][pn]
+  double* Es = ring + 2 * D * pn;          // [pe]
+  double* Fs = Es + pe;                    // [D][2][NCP][pe]
+
+  const int n0 = g.n[0], n1 = g.n[1], n2 = (D == 3 ? g.n[2] : 1);
+  const int64_t plane = (int64_t)n1 * n2;
+  const int t1 = blockIdx.x % mg.tiles1, t2 = blockIdx.x / mg.tiles1;
+  const int i1s = t1 * mg.P1, i2s = (D == 3 ? t2 * mg.P2 : 0);
+  const int L0 = blockIdx.y * mg.seg;
+  const int W1 = mg.P1 + 2, W2 = (D == 3 ? mg.P2 + 2 : 1);   // halo tile dims (nodes)
+  const int E1 = mg.P1 + 1, E2 = (D == 3 ? mg.P2 + 1 : 1);   // element tile dims
+  const double* xb = HAS_X ? x + (int64_t)b * fstride : nullptr;
+  double* yb = y + (int64_t)b * fstride;
+  StrainShift sh;
+  if (SHIFT) sh = shifts[b];
+
+  // thread -> owned in-plane node
+  const int tid = threadIdx.x;
+  const int own1 = (D == 3 ? tid / mg.P2 : tid), own2 = (D == 3 ? tid % mg.P2 : 0);
+  const bool owner = tid < mg.P1 * (D == 3 ? mg.P2 : 1);
+
+  auto load_layer = [&](int layer, int slot) {
+    const int l = ((layer % n0) + n0) % n0;
+    for (int idx = tid; idx < pn; idx += blockDim.x) {
+      const int h1 = idx / W2, h2 = idx % W2;
+      const int gi1 = (i1s - 1 + h1 + n1) % n1;
+      const int gi2 = (D == 3 ? (i2s - 1 + h2 + n2) % n2 : 0);
+      const int64_t node = (int64_t)l * plane + (int64_t)gi1 * n2 + gi2;
+#pragma unroll
+      for (int a = 0; a < D; ++a) ring[(slot * D + a) * pn + idx] = HAS_X ? xb[a * g.N + node] : 0.0;
+    }
+  };
+
+  double carry[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) carry[a] = 0.0;
+  double dot = 0.0;
+
+  if (HAS_X) load_layer(L0 - 1, (L0 - 1) & 1);
+  for (int e0 = L0 - 1; e0 < L0 + mg.seg; ++e0) {
+    if (HAS_X) load_layer(e0 + 1, (e0 + 1) & 1);
+    if (HAS_E) {
+      const int l = ((e0 % n0) + n0) % n0;
+      for (int idx = tid; idx < pe; idx += blockDim.x) {
+        const int h1 = idx / E2, h2 = idx % E2;
+        const int gi1 = (i1s - 1 + h1 + n1) % n1;
+        const int gi2 = (D == 3 ? (i2s - 1 + h2 + n2) % n2 : 0);
+        Es[idx] = E[(int64_t)l * plane + (int64_t)gi1 * n2 + gi2];
+      }
+    }
+    __syncthreads();
+    const int s0 = e0 & 1, s1 = (e0 + 1) & 1;
+    for (int idx = tid; idx < pe; idx += blockDim.x) {
+      const int h1 = idx / E2, h2 = idx % E2;
+      double u[D][NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int o0 = (c >> (D - 1)) & 1;
+        const int o1 = (c >> (D - 2)) & 1;
+        const int o2 = (D == 3 ? c & 1 : 0);
+        const int node = (h1 + o1) * W2 + (h2 + o2);
+#pragma unroll
+        for (int a = 0; a < D; ++a) u[a][c] = HAS_X ? ring[((o0 ? s1 : s0) * D + a) * pn + node] : 0.0;
+      }
+      const double Ee = HAS_E ? Es[idx] : e_uniform;
+      element_force<D, double, SHIFT>(ec, &sh, u, Ee);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int o0 = (c >> (D - 1)) & 1;
+        const int cin = c & (NCP - 1);
+#pragma unroll
+        for (int a = 0; a < D; ++a) Fs[((a * 2 + o0) * NCP + cin) * pe + idx] = u[a][c];
+      }
+    }
+    __syncthreads();
+    if (owner) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        double add0 = 0.0, add1 = 0.0;
+#pragma unroll
+        for (int cin = 0; cin < NCP; ++cin) {
+          const int o1 = (D == 3 ? (cin >> 1) & 1 : cin & 1);
+          const int o2 = (D == 3 ? cin & 1 : 0);
+          const int el = (own1 + 1 - o1) * E2 + (D == 3 ? own2 + 1 - o2 : 0);
+          add0 += Fs[((a * 2 + 0) * NCP + cin) * pe + el];
+          add1 += Fs[((a * 2 + 1) * NCP + cin) * pe + el];
+        }
+        if (e0 >= L0) {
+          const double q = sgn * (carry[a] + add0);
+          const int l = e0;  // < n0 by construction
+          const int64_t node = (int64_t)l * plane + (int64_t)(i1s + own1) * n2 + (D == 3 ? i2s + own2 : 0);
+          yb[a * g.N + node] = q;
+          if (DOT == 1) dot += ring[(s0 * D + a) * pn + (own1 + 1) * W2 + (D == 3 ? own2 + 1 : 0)] * q;
+          if (DOT == 2) dot += q * q;
+        }
+        carry[a] = add1;
+      }
+    }
+    __syncthreads();
+  }
+  if (DOT) {
+    const double s = block_sum(dot);
+    if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
+  }
+}
+
+template <int D> static MarchGeom march_geom(const Grid& g) {
+  MarchGeom m;
+  if (D == 2) {
+    m.P1 = std::min(g.n[1], 256);
+    m.P2 = 1;
+  } else {
+    m.P2 = std::min(g.n[2], 32);
+    m.P1 = std::min(g.n[1], 256 / m.P2);
+  }
+  m.tiles1 = g.n[1] / m.P1;
+  m.tiles2 = (D == 3 ? g.n[2] / m.P2 : 1);
+  const int tiles = m.tiles1 * m.tiles2;
+  int seg = std::min(g.n[0], 16);
+  while ((int64_t)tiles * (g.n[0] / seg) > kMaxPartials) seg *= 2;
+  m.seg = seg;
+  return m;
+}
+
+template <int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
+static cudaError_t apply_K_t(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
+                             double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, double* partial,
+                             int* nparts, const CgState* cg, cudaStream_t st) {
+  MarchGeom m = march_geom<D>(g);
+  const size_t smem = march_smem<D>(m);
+  auto kern = k_apply_K<D, DOT, HAS_X, HAS_E, SHIFT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, nb);
+  // one element per thread per layer; warps round up (owners are the first P1*P2)
+  const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;
+  const char* kname = DOT == 1 ? "apply_K"
+                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
+  JFFT_K(kname, st, kern<<<grid, threads, smem, st>>>(g, m, ec, E, e_uniform, x, y, fstride, shifts, sgn, partial, cg));
+  if (nparts) *nparts = grid.x * grid.y;
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
+                             double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, int dot_mode,
+                             double* partial, int* nparts, const CgState* cg, cudaStream_t st) {
+  const bool hx = x != nullptr, he = E != nullptr, sh = shifts != nullptr;
+#define JFFT_AK(DOT, HX, HE, SH) \
+  if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
+    return apply_K_t<D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st);
+  JFFT_AK(1, true, true, false)   // CG: q = K p, p.q
+  JFFT_AK(0, true, true, false)   // plain apply
+  JFFT_AK(0, true, false, false)  // reference operator (uniform E)
+  JFFT_AK(2, false, true, true)   // load: f = -B^T W C eps_bar, ||f||^2
+  JFFT_AK(2, true, true, true)    // true residual, ||r||^2
+  JFFT_AK(0, false, true, true)
+  JFFT_AK(0, true, true, true)
+#undef JFFT_AK
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
+                           double* y, int nb, int64_t field_stride, const StrainShift* shifts, double sgn, int dot_mode,
+                           double* partial, int* nparts, const CgState* done, cudaStream_t st) {
+  if (g.d == 2)
+    return apply_K_d<2>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st);
+  return apply_K_d<3>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st);
+}
+
+// ------------------------------------------------------------------ S8
+template <int D>
+__global__ void __launch_bounds__(256) k_stress(Grid g, ElemConst ec, const double* __restrict__ E,
+                                                const double* __restrict__ u, const StrainShift* __restrict__ shifts,
+                                                double* __restrict__ stress, double* __restrict__ partial) {
+  constexpr int NC = 1 << D;
+  constexpr int DS = D * (D + 1) / 2;
+  const int b = blockIdx.y;
+  const double* ub = u + (int64_t)b * D * g.N;
+  double acc[DS];
+#pragma unroll
+  for (int s = 0; s < DS; ++s) acc[s] = 0.0;
+  const StrainShift sh = shifts[b];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.N; e += (int64_t)gridDim.x * blockDim.x) {
+    int idx[3];
+    int64_t r = e;
+    for (int a = D - 1; a >= 0; --a) { idx[a] = (int)(r % g.n[a]); r /= g.n[a]; }
+    double uc[D][NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      int64_t node = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int o = (c >> (D - 1 - a)) & 1;
+        node = node * g.n[a] + (idx[a] + o) % g.n[a];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) uc[a][c] = ub[a * g.N + node];
+    }
+    double sig[6];
+    element_stress<D>(ec, &sh, uc, E[e], sig);
+#pragma unroll
+    for (int s = 0; s < DS; ++s) {
+      if (stress) stress[((int64_t)b * DS + s) * g.N + e] = sig[s];
+      acc[s] += sig[s];
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < DS; ++s) {
+    const double v = block_sum(acc[s]);
+    if (threadIdx.x == 0) partial[((int64_t)b * DS + s) * kMaxPartials + blockIdx.x] = v * ec.vol;
+  }
+}
+
+cudaError_t launch_stress(const Grid& g, const ElemConst& ec, const double* E, const double* u, int nb,
+                          const StrainShift* shifts, double* stress, double* partial, int* nparts, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.N + 255) / 256, 1024);
+  dim3 grid(blocks, nb);
+  if (g.d == 2) JFFT_K("stress", st, k_stress<2><<<grid, 256, 0, st>>>(g, ec, E, u, shifts, stress, partial));
+  else JFFT_K("stress", st, k_stress<3><<<grid, 256, 0, st>>>(g, ec, E, u, shifts, stress, partial));
+  *nparts = blocks;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ S5
+template <int D>
+__global__ void k_node_esum(Grid g, const double* __restrict__ E, double* __restrict__ esum) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x) {
+    int idx[3];
+    int64_t r = i;
+    for (int a = D - 1; a >= 0; --a) { idx[a] = (int)(r % g.n[a]); r /= g.n[a]; }
+    double s = 0.0;
+    for (int c = 0; c < (1 << D); ++c) {
+      int64_t e = 0;
+      for (int a = 0; a < D; ++a) {
+        const int o = (c >> (D - 1 - a)) & 1;
+        e = e * g.n[a] + (idx[a] - o + g.n[a]) % g.n[a];
+      }
+      s += E[e];
+    }
+    esum[i] = s;
+  }
+}
+
+cudaError_t launch_node_esum(const Grid& g, const double* E, double* esum, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.N + 255) / 256, 152 * 16);
+  if (g.d == 2) JFFT_K("node_esum", st, k_node_esum<2><<<blocks, 256, 0, st>>>(g, E, esum));
+  else JFFT_K("node_esum", st, k_node_esum<3><<<blocks, 256, 0, st>>>(g, E, esum));
+  return cudaGetLastError();
+}
+
+__global__ void k_jacobi_half(const double* __restrict__ esum, double* __restrict__ js, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = esum[i];
+    js[i] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  }
+}
+
+cudaError_t launch_jacobi_half(const double* esum, double* js, int64_t N, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
+  JFFT_K("jacobi_half", st, k_jacobi_half<<<blocks, 256, 0, st>>>(esum, js, N));
+  return cudaGetLastError();
+}
+
+struct Kappa3 { double k[3]; };
+
+__global__ void k_diag_closed(Grid g, const double* __restrict__ esum, Kappa3 kap, double* __restrict__ diag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = esum[i];
+    for (int a = 0; a < g.d; ++a) diag[a * g.N + i] = kap.k[a] * s;
+  }
+}
+
+cudaError_t launch_diag_closed(const Grid& g, const double* esum, const double* kappa3, double* diag,
+                               cudaStream_t st) {
+  Kappa3 k;
+  for (int a = 0; a < 3; ++a) k.k[a] = kappa3[a];
+  const int blocks = (int)std::min<int64_t>((g.N + 255) / 256, 152 * 16);
+  JFFT_K("diag_closed", st, k_diag_closed<<<blocks, 256, 0, st>>>(g, esum, k, diag));
+  return cudaGetLastError();
+}
+
+// Alg. 2: comb teeth of component `comp` sit at nodes whose 0-based index along
+// every axis a has parity 1 - off_a (1-based index 2 I_a - off_a).
+__device__ inline bool on_comb(const Grid& g, int64_t i, int offbits) {
+  int64_t r = i;
+  bool on = true;
+  for (int a = g.d - 1; a >= 0; --a) {
+    const int ia = (int)(r % g.n[a]);
+    r /= g.n[a];
+    const int off = (offbits >> (g.d - 1 - a)) & 1;
+    on = on && ((ia & 1) == 1 - off);
+  }
+  return on;
+}
+
+__global__ void k_fill_comb(Grid g, int comp, int offbits, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N * g.d; i += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(i / g.N);
+    const int64_t node = i % g.N;
+    x[i] = (a == comp && on_comb(g, node, offbits)) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_extract_comb(Grid g, int comp, int offbits, const double* __restrict__ y, double* __restrict__ diag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.N; i += (int64_t)gridDim.x * blockDim.x)
+    if (on_comb(g, i, offbits)) diag[comp * g.N + i] = y[comp * g.N + i];
+}
+
+cudaError_t launch_fill_comb(const Grid& g, int comp, int offbits, double* x, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.N * g.d + 255) / 256, 152 * 16);
+  JFFT_K("fill_comb", st, k_fill_comb<<<blocks, 256, 0, st>>>(g, comp, offbits, x));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_comb(const Grid& g, int comp, int offbits, const double* y, double* diag, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.N + 255) / 256, 152 * 16);
+  JFFT_K("extract_comb", st, k_extract_comb<<<blocks, 256, 0, st>>>(g, comp, offbits, y, diag));
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ S9 (Alg. 1)
+// Field alpha of the batch [d][d][N] is the unit impulse in component alpha at node 0.
+__global__ void k_impulses(Grid g, double* __restrict__ x) {
+  const int64_t total = (int64_t)g.d * g.d * g.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t field = i / ((int64_t)g.d * g.N);
+    const int64_t rem = i % ((int64_t)g.d * g.N);
+    x[i] = (rem == field * g.N) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t launch_impulses(const Grid& g, double* x, cudaStream_t st) {
+  const int64_t total = (int64_t)g.d * g.d * g.N;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  JFFT_K("impulses", st, k_impulses<<<blocks, 256, 0, st>>>(g, x));
+  return cudaGetLastError();
+}
+
+// Step 3 of Alg. 1: invert the d x d block at every stored frequency; zero frequency
+// set to 0. spec holds our forward transform (2 x the unnormalised DFT) of the
+// responses R[alpha][beta]; the table stores G_hat * scale_store, upper triangle
+// in the order (00, 01, 11) / (00, 01, 02, 11, 12, 22).
+template <int D>
+__global__ void k_green_table(Grid g, const double2* __restrict__ spec, double* __restrict__ G, double scale_store) {
+  constexpr int NCMP = D * (D + 1) / 2;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < g.F; f += (int64_t)gridDim.x * blockDim.x) {
+    double K[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) K[a][b] = 0.5 * spec[((int64_t)a * D + b) * g.F + f].x;
+    // symmetrise (the symbol is real symmetric; this removes rounding asymmetry)
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = a + 1; b < D; ++b) { const double s = 0.5 * (K[a][b] + K[b][a]); K[a][b] = K[b][a] = s; }
+    double out[NCMP];
+    if (f == 0) {
+#pragma unroll
+      for (int c = 0; c < NCMP; ++c) out[c] = 0.0;
+    } else if (D == 2) {
+      const double det = K[0][0] * K[1][1] - K[0][1] * K[1][0];
+      out[0] = K[1][1] / det;
+      out[1] = -K[0][1] / det;
+      out[2] = K[0][0] / det;
+    } else {
+      const double c00 = K[1][1] * K[2][2] - K[1][2] * K[2][1];
+      const double c01 = K[0][2] * K[2][1] - K[0][1] * K[2][2];
+      const double c02 = K[0][1] * K[1][2] - K[0][2] * K[1][1];
+      const double c11 = K[0][0] * K[2][2] - K[0][2] * K[2][0];
+      const double c12 = K[0][2] * K[1][0] - K[0][0] * K[1][2];
+      const double c22 = K[0][0] * K[1][1] - K[0][1] * K[1][0];
+      const double det = K[0][0] * c00 + K[0][1] * (K[1][2] * K[2][0] - K[1][0] * K[2][2]) + K[0][2] * (K[1][0] * K[2][1] - K[1][1] * K[2][0]);
+      out[0] = c00 / det; out[1] = c01 / det; out[2] = c02 / det;
+      out[3] = c11 / det; out[4] = c12 / det; out[5] = c22 / det;
+    }
+#pragma unroll
+    for (int c = 0; c < NCMP; ++c) G[f * NCMP + c] = out[c] * scale_store;
+  }
+}
+
+cudaError_t launch_green_table(const Grid& g, const double2* spec, double* G, double scale_store, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.F + 255) / 256, 152 * 16);
+  if (g.d == 2) JFFT_K("green_table", st, k_green_table<2><<<blocks, 256, 0, st>>>(g, spec, G, scale_store));
+  else JFFT_K("green_table", st, k_green_table<3><<<blocks, 256, 0, st>>>(g, spec, G, scale_store));
+  return cudaGetLastError();
+}
+
+template <int D>
+__global__ void k_green_export(Grid g, const double* __restrict__ G, double* __restrict__ out, double inv_scale) {
+  constexpr int NCMP = D * (D + 1) / 2;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < g.F; f += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        const int c = (D == 2) ? (lo == 0 ? hi : 2) : (lo == 0 ? hi : (lo == 1 ? 2 + hi : 5));
+        out[(f * D + a) * D + b] = G[f * NCMP + c] * inv_scale;
+      }
+  }
+}
+
+cudaError_t launch_green_export(const Grid& g, const double* G, double* out, double scale_store, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.F + 255) / 256, 152 * 16);
+  if (g.d == 2) JFFT_K("green_export", st, k_green_export<2><<<blocks, 256, 0, st>>>(g, G, out, 1.0 / scale_store));
+  else JFFT_K("green_export", st, k_green_export<3><<<blocks, 256, 0, st>>>(g, G, out, 1.0 / scale_store));
+  return cudaGetLastError();
+}
+
+}  // namespace jfft

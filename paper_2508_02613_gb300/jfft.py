@@ -1,0 +1,303 @@
+"""ctypes binding of libjfft (include/jfft.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts NumPy arrays
+(host io mode) or CUDA tensor pointers (device io mode) to the C ABI and raises
+``JfftError`` on failure. There is no CPU fallback: if the library is missing or
+cannot be loaded, ``load()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_size_t, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+JFFT_OK, JFFT_ERR_ARG, JFFT_ERR_OOM, JFFT_ERR_CUDA = 0, 1, 2, 3
+JFFT_ERR_NOCONV, JFFT_ERR_BREAKDOWN, JFFT_ERR_TIMEOUT, JFFT_ERR_UNSUPPORTED = 4, 5, 6, 7
+PRECOND = {"none": -1, "green": 0, "green_jacobi": 1, "jacobi": 2}
+MATERIAL = {"young": 0, "density": 1}
+STOP = {"rel": 0, "abs_sq": 1}
+MEM = {"host": 0, "device": 1}
+DIAG = {"closed_form": 0, "combs": 1}
+
+
+class JfftGrid(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int64 * 3)]
+
+
+class JfftMaterial(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("field", POINTER(c_double)), ("nu", c_double), ("e_min", c_double),
+                ("e_max", c_double), ("exponent", c_double)]
+
+
+class JfftOptions(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("max_iter", c_int), ("stop_mode", c_int), ("stream", c_void_p),
+                ("hbm_budget", c_size_t), ("check_every", c_int), ("io_memory", c_int), ("max_loads", c_int),
+                ("void_value", c_double), ("device", c_int)]
+
+
+class JfftResult(ctypes.Structure):
+    _fields_ = [("u", c_void_p), ("stress", c_void_p), ("C_hom", c_void_p), ("iters", c_void_p),
+                ("rel_res", c_void_p)]
+
+
+class JfftError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"jfft status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+_SIGNATURES = {
+    "jfft_default_options": (None, [POINTER(JfftOptions)]),
+    "jfft_create": (c_int, [POINTER(c_void_p), POINTER(JfftGrid), POINTER(JfftMaterial), c_void_p,
+                            POINTER(JfftOptions)]),
+    "jfft_set_material": (c_int, [c_void_p, POINTER(JfftMaterial)]),
+    "jfft_solve": (c_int, [c_void_p, c_int, c_void_p, c_double, c_int, POINTER(JfftResult)]),
+    "jfft_destroy": (None, [c_void_p]),
+    "jfft_status_string": (c_char_p, [c_int]),
+    "jfft_last_error": (c_char_p, [c_void_p]),
+    "jfft_set_io_memory": (c_int, [c_void_p, c_int]),
+    "jfft_set_max_iter": (c_int, [c_void_p, c_int]),
+    "jfft_get_material": (c_int, [c_void_p, c_void_p]),
+    "jfft_rhs": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "jfft_apply_K": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "jfft_get_diag": (c_int, [c_void_p, c_int, c_void_p]),
+    "jfft_get_green": (c_int, [c_void_p, c_void_p]),
+    "jfft_apply_precond": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "jfft_solve_rhs": (c_int, [c_void_p, c_int, c_void_p, c_double, c_int, c_void_p, c_void_p]),
+    "jfft_postprocess": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jfft_launch_count": (c_int64, [c_void_p]),
+    "jfft_set_profiling": (c_int, [c_void_p, c_int]),
+    "jfft_profile_json": (c_char_p, [c_void_p]),
+    "jfft_workspace_bytes": (c_size_t, [c_void_p]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libjfft.so (built in-tree by ``build.build()``); raises if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"libjfft.so not built at {path}; run paper_2508_02613_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/jfft.h."""
+    hdr = os.path.join(_build.INCLUDE, "jfft.h")
+    src = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:[\w\*]+\s+)+\**(jfft_\w+)\s*\(", src, re.M)))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(c_void_p)
+    if hasattr(a, "data_ptr"):
+        return c_void_p(a.data_ptr())
+    raise TypeError(type(a))
+
+
+def _f64(a, shape=None):
+    out = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        out = out.reshape(shape)
+    return out
+
+
+class Solver:
+    """One grid + material; methods mirror the C calls of the same name."""
+
+    def __init__(self, shape, field, nu, kind="young", e_min=0.0, e_max=1.0, exponent=1.0, C_ref=None,
+                 max_iter=100000, stop_mode="rel", stream=None, check_every=8, io="host", max_loads=6,
+                 void_value=1.0, device=0, hbm_budget=0, pinned=False):
+        self.lib = load()
+        self.pinned = pinned
+        self.shape = tuple(int(s) for s in shape)
+        self.d = len(self.shape)
+        self.ds = self.d * (self.d + 1) // 2
+        self.N = int(np.prod(self.shape))
+        self.io = io
+        g = JfftGrid(self.d, (c_int64 * 3)(*(list(self.shape) + [0] * (3 - self.d))))
+        self._field = _f64(field).reshape(-1)
+        mat = JfftMaterial(MATERIAL[kind], self._field.ctypes.data_as(POINTER(c_double)), nu, e_min, e_max, exponent)
+        self._mat_args = (kind, nu, e_min, e_max, exponent)
+        opt = JfftOptions()
+        self.lib.jfft_default_options(ctypes.byref(opt))
+        opt.max_iter = max_iter
+        opt.stop_mode = STOP[stop_mode]
+        opt.stream = c_void_p(stream) if stream else None
+        opt.check_every = check_every
+        opt.io_memory = MEM[io]
+        opt.max_loads = max_loads
+        opt.void_value = void_value
+        opt.device = device
+        opt.hbm_budget = hbm_budget
+        self.max_loads = max(max_loads, self.d)
+        h = c_void_p()
+        cref = None if C_ref is None else _f64(C_ref).reshape(-1)
+        st = self.lib.jfft_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(mat), _ptr(cref), ctypes.byref(opt))
+        if st != JFFT_OK:
+            msg = self.lib.jfft_last_error(None) or self.lib.jfft_status_string(st)
+            raise JfftError(st, msg.decode() if isinstance(msg, bytes) else msg)
+        self.h = h
+
+    # -- plumbing
+    def _check(self, st, allow=()):
+        if st != JFFT_OK and st not in allow:
+            raise JfftError(st, self.lib.jfft_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.jfft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, shape, dtype=np.float64):
+        if self.io == "host":
+            if self.pinned:
+                import torch
+                tdt = torch.float64 if dtype == np.float64 else torch.int32
+                return torch.empty(shape, dtype=tdt, pin_memory=True).numpy()
+            return np.empty(shape, dtype=dtype)
+        import torch
+        tdt = torch.float64 if dtype == np.float64 else torch.int32
+        return torch.empty(shape, dtype=tdt, device="cuda")
+
+    def _in(self, a, shape):
+        if self.io == "host":
+            return _f64(a, shape)
+        return a
+
+    # -- calls
+    def set_material(self, field, e_min=None, e_max=None, exponent=None):
+        """New material field (host array, or a CUDA tensor in device io mode); the
+        density map parameters may change, the kind and nu may not."""
+        kind, nu, e_min0, e_max0, exponent0 = self._mat_args
+        e_min = e_min0 if e_min is None else e_min
+        e_max = e_max0 if e_max is None else e_max
+        exponent = exponent0 if exponent is None else exponent
+        self._mat_args = (kind, nu, e_min, e_max, exponent)
+        if self.io == "host":
+            self._field = _f64(field).reshape(-1)
+            fptr = self._field.ctypes.data_as(POINTER(c_double))
+        else:
+            self._field = field
+            fptr = ctypes.cast(c_void_p(field.data_ptr()), POINTER(c_double))
+        mat = JfftMaterial(MATERIAL[kind], fptr, nu, e_min, e_max, exponent)
+        self._check(self.lib.jfft_set_material(self.h, ctypes.byref(mat)))
+
+    def set_io_memory(self, io):
+        self._check(self.lib.jfft_set_io_memory(self.h, MEM[io]))
+        self.io = io
+
+    def set_max_iter(self, m):
+        self._check(self.lib.jfft_set_max_iter(self.h, int(m)))
+
+    def solve(self, eps_bar, tol, precond="green_jacobi", want_u=True, want_stress=True):
+        eps = np.atleast_2d(_f64(eps_bar)) if self.io == "host" else eps_bar
+        nl = int(eps.shape[0])
+        u = self._out((nl, self.d) + self.shape) if want_u else None
+        stress = self._out((nl, self.ds) + self.shape) if want_stress else None
+        chom = self._out((self.ds, nl))
+        its = self._out((nl,), np.int32)
+        rel = self._out((nl,))
+        res = JfftResult(_ptr(u), _ptr(stress), _ptr(chom), _ptr(its), _ptr(rel))
+        st = self._check(self.lib.jfft_solve(self.h, nl, _ptr(eps), float(tol), PRECOND[precond], ctypes.byref(res)),
+                         allow=(JFFT_ERR_NOCONV, JFFT_ERR_BREAKDOWN))
+        return {"u": u, "stress": stress, "C_hom": chom, "iters": its, "rel_res": rel, "status": st}
+
+    def get_material(self):
+        E = self._out(self.shape)
+        self._check(self.lib.jfft_get_material(self.h, _ptr(E)))
+        return E
+
+    def rhs(self, eps_bar):
+        eps = np.atleast_2d(_f64(eps_bar)) if self.io == "host" else eps_bar
+        f = self._out((int(eps.shape[0]), self.d) + self.shape)
+        self._check(self.lib.jfft_rhs(self.h, int(eps.shape[0]), _ptr(eps), _ptr(f)))
+        return f
+
+    def apply_K(self, x):
+        x = self._in(x, (-1, self.d) + self.shape)
+        y = self._out(tuple(x.shape))
+        self._check(self.lib.jfft_apply_K(self.h, int(x.shape[0]), _ptr(x), _ptr(y)))
+        return y
+
+    def get_diag(self, method="closed_form"):
+        out = self._out((self.d,) + self.shape)
+        self._check(self.lib.jfft_get_diag(self.h, DIAG[method], _ptr(out)))
+        return out
+
+    def get_green(self):
+        F = self.N // self.shape[-1] * (self.shape[-1] // 2 + 1)
+        out = self._out((F, self.d, self.d))
+        self._check(self.lib.jfft_get_green(self.h, _ptr(out)))
+        return out
+
+    def apply_precond(self, precond, r):
+        r = self._in(r, (-1, self.d) + self.shape)
+        z = self._out(tuple(r.shape))
+        self._check(self.lib.jfft_apply_precond(self.h, PRECOND[precond], int(r.shape[0]), _ptr(r), _ptr(z)))
+        return z
+
+    def solve_rhs(self, f, tol, precond="green_jacobi"):
+        f = self._in(f, (-1, self.d) + self.shape)
+        nb = int(f.shape[0])
+        u = self._out(tuple(f.shape))
+        its = self._out((nb,), np.int32)
+        st = self._check(self.lib.jfft_solve_rhs(self.h, nb, _ptr(f), float(tol), PRECOND[precond], _ptr(u), _ptr(its)),
+                         allow=(JFFT_ERR_NOCONV, JFFT_ERR_BREAKDOWN))
+        return {"u": u, "iters": its, "status": st}
+
+    def postprocess(self, eps_bar, u):
+        eps = np.atleast_2d(_f64(eps_bar)) if self.io == "host" else eps_bar
+        nl = int(eps.shape[0])
+        u = self._in(u, (nl, self.d) + self.shape)
+        stress = self._out((nl, self.ds) + self.shape)
+        chom = self._out((self.ds, nl))
+        self._check(self.lib.jfft_postprocess(self.h, nl, _ptr(eps), _ptr(u), _ptr(stress), _ptr(chom)))
+        return {"stress": stress, "C_hom": chom}
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.jfft_launch_count(self.h))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.lib.jfft_workspace_bytes(self.h))
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.jfft_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self) -> dict:
+        import json
+        return json.loads(self.lib.jfft_profile_json(self.h).decode())

@@ -107,7 +107,10 @@ def cosine_density(shape, chi_tot: float) -> np.ndarray:
 
 
 def random_field(shape, seed: int, zero_mean: bool = False) -> np.ndarray:
-    """Standard-normal array of the given shape (e.g. [d, n_1, ..., n_d])."""
+    """Standard-normal array of the given shape (e.g. [d, n_1, ..., n_d]).
+
+    ``zero_mean`` subtracts the mean over every axis but the first, so a [d, *n]
+    field gets zero mean per component."""
     rng = np.random.default_rng(seed)
     a = rng.standard_normal(tuple(int(s) for s in shape))
     if zero_mean:

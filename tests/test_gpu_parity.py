@@ -1,0 +1,282 @@
+"""GPU parity of every step of the path against the FP64 oracle, through the C ABI.
+
+Tolerances (FP64 everywhere; the GPU uses FMA and tree reductions, the oracle
+sequential NumPy/SciPy):
+  * single operator / preconditioner applications: 1e-13 relative (a few ulps of
+    the O(10)-term sums, amplified by at most log2 N FFT stages);
+  * PCG iterates at the same iteration count k <= 10: 1e-12 (before the CG
+    recurrence starts amplifying rounding, see tests/test_oracle_pcg.py);
+  * converged solves: displacement 1e-10, homogenised stiffness 1e-9 relative;
+  * runs stopped at tolerance tau: iteration counts within one, displacement within
+    10 tau of the oracle's (the oracle-vs-oracle floor is ~tau).
+Grids are powers of two (the FFT's requirement here), so "ragged" coverage comes
+from the smallest grids (4 per axis), non-square grids and tile-count edge cases.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import assemble, dense, fe, green, material, pcg, post, solve as osolve
+from synthetic import cosine_density, laminate_density, mandel_unit_loads, random_field, smooth_density
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _solver(shape, rho, contrast=1e4, exponent=2.0, nu=0.3, **kw):
+    from paper_2508_02613_gb300.jfft import Solver
+    return Solver(shape, rho, nu, kind="density", e_min=1.0 / contrast, e_max=1.0, exponent=exponent, **kw)
+
+
+def _problem(shape, seed=0, contrast=1e4, exponent=2.0, modes=8, kmax=3.0):
+    rho = smooth_density(shape, modes, kmax, seed)
+    E = material.young_from_density(rho, 1.0 / contrast, 1.0, exponent)
+    return rho, E
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+SHAPES = [(4, 4), (8, 16), (16, 8), (64, 512), (4, 4, 4), (8, 4, 16), (16, 16, 64)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_material_and_operator(shape):
+    d = len(shape)
+    rho, E = _problem(shape, 1)
+    s = _solver(shape, rho)
+    assert rel(s.get_material(), E) <= 4e-16
+    K = assemble.assemble_K(shape, E, fe.C_unit(d, 0.3))
+    x = random_field((2, d) + shape, 3)
+    y = s.apply_K(x)
+    want = np.stack([assemble.apply(K, x[i]) for i in range(2)])
+    assert rel(y, want) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_rhs(shape):
+    d = len(shape)
+    rho, E = _problem(shape, 2)
+    s = _solver(shape, rho)
+    ds = d * (d + 1) // 2
+    eps = np.vstack([np.eye(ds)[:2], np.linspace(-1, 1, ds)])
+    f = s.rhs(eps)
+    for i in range(3):
+        assert rel(f[i], assemble.assemble_rhs(shape, E, fe.C_unit(d, 0.3), eps[i])) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (4, 16), (8, 4, 8), (16, 16, 64)])
+def test_jacobi_diagonal_closed_form_and_alg2(shape):
+    d = len(shape)
+    rho, E = _problem(shape, 3)
+    s = _solver(shape, rho)
+    K = assemble.assemble_K(shape, E, fe.C_unit(d, 0.3))
+    want = K.diagonal().reshape((d,) + shape)
+    assert rel(s.get_diag("closed_form"), want) <= 1e-14
+    assert rel(s.get_diag("combs"), want) <= 1e-14
+
+
+def _half_spectrum(G_hat, shape):
+    """Oracle symbol [d][d][k_0..k_{d-1}] -> the library's order [F][d][d] (k_0 fastest,
+    last axis halved)."""
+    d = len(shape)
+    M = shape[-1] // 2
+    g = np.moveaxis(G_hat.real, (0, 1), (-2, -1))[..., : M + 1, :, :]
+    axes = tuple(range(d))[::-1] + (d, d + 1)
+    return np.transpose(g, axes).reshape(-1, d, d)
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (16, 4), (4, 8, 16), (8, 8, 8)])
+def test_green_symbol_alg1(shape):
+    d = len(shape)
+    rho, E = _problem(shape, 4)
+    s = _solver(shape, rho)
+    _, G_hat = green.green_symbol(shape, E.mean() * fe.C_unit(d, 0.3))
+    assert rel(s.get_green(), _half_spectrum(G_hat, shape)) <= symbol_tol(shape)
+
+
+def symbol_tol(shape):
+    """Alg. 1 obtains K_hat by transforming impulse responses whose O(1) entries cancel to
+    O(theta^2) at the lowest frequency theta_min = 2 pi / n_max, so each side's symbol
+    carries a relative rounding error of order eps (n_max / 2 pi)^2 there, and the Green
+    operator's output is dominated by those frequencies."""
+    eps = np.finfo(np.float64).eps
+    return max(1e-13, 20 * eps * (max(shape) / (2 * np.pi)) ** 2)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("pc", ["green", "green_jacobi", "jacobi"])
+def test_preconditioners(shape, pc):
+    d = len(shape)
+    rho, E = _problem(shape, 5)
+    s = _solver(shape, rho)
+    prob = osolve.setup(shape, E, 0.3)
+    r = random_field((2, d) + shape, 6)
+    z = s.apply_precond(pc, r)
+    minv = prob.minv(pc)
+    want = np.stack([minv(r[i]) for i in range(2)])
+    assert rel(z, want) <= (symbol_tol(shape) if pc != "jacobi" else 1e-15)
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (8, 8, 8)])
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+def test_homogeneous_one_iteration(shape, pc):
+    from paper_2508_02613_gb300.jfft import Solver
+    d = len(shape)
+    C_ref = 0.6 * fe.C_unit(d, 0.3)
+    s = Solver(shape, np.full(shape, 3.7), 0.3, C_ref=C_ref)
+    f = random_field((d,) + shape, 7, zero_mean=True)[None]  # zero mean per component
+    out = s.solve_rhs(f, 1e-12, pc)
+    assert int(out["iters"][0]) == 1
+    prob = osolve.setup(shape, np.full(shape, 3.7), 0.3, C_ref=C_ref)
+    want = dense.dense_solve(prob.K, f[0]) if np.prod(shape) <= 512 else None
+    if want is not None:
+        assert np.linalg.norm(post.remove_mean(out["u"][0]) - want) <= 1e-11 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("shape", [(32, 32), (8, 8, 8)])
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+def test_same_k_iterates(shape, pc):
+    d = len(shape)
+    rho, E = _problem(shape, 8, contrast=1e4)
+    s = _solver(shape, rho)
+    prob = osolve.setup(shape, E, 0.3)
+    f = assemble.assemble_rhs(shape, E, prob.C, mandel_unit_loads(d)[0])
+    for k in (1, 3, 10):
+        s.set_max_iter(k)
+        out = s.solve_rhs(f[None], 0.0, pc)
+        assert int(out["iters"][0]) == k
+        ref = pcg.pcg(prob.apply_K, prob.minv(pc), f, 0.0, k)
+        assert np.linalg.norm(out["u"][0] - ref.x) <= 1e-12 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4)])
+@pytest.mark.parametrize("pc", ["green", "green_jacobi", "jacobi", "none"])
+def test_converged_vs_dense(shape, pc):
+    d = len(shape)
+    rho, E = _problem(shape, 9, contrast=1e3)
+    s = _solver(shape, rho, contrast=1e3)
+    prob = osolve.setup(shape, E, 0.3)
+    eps = mandel_unit_loads(d)[-1:]
+    out = s.solve(eps, 1e-13, pc)
+    f = assemble.assemble_rhs(shape, E, prob.C, eps[0])
+    want = dense.dense_solve(prob.K, f)
+    assert np.linalg.norm(out["u"][0] - want) <= 1e-10 * np.linalg.norm(want)
+    C_want = post.homogenised_stress(shape, E, prob.C, eps[0], want)
+    assert rel(out["C_hom"][:, 0], C_want) <= 1e-9
+    assert out["rel_res"][0] <= 1e-12
+
+
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+def test_small_workload_32x32(pc):
+    """The 32 x 32 workload: 16 Fourier modes |k| <= 4, E = 1e-4 + (1 - 1e-4) rho^2,
+    nu = 0.3, eps_xx = 1, tolerance 1e-6, C_ref = mean material."""
+    shape = (32, 32)
+    rho = smooth_density(shape, 16, 4.0, 0)
+    E = material.young_from_density(rho, 1e-4, 1.0, 2.0)
+    s = _solver(shape, rho)
+    eps = mandel_unit_loads(2)[:1]
+    out = s.solve(eps, 1e-6, pc)
+    prob = osolve.setup(shape, E, 0.3)
+    ref = osolve.solve(prob, eps, 1e-6, pc)
+    assert abs(int(out["iters"][0]) - int(ref.iters[0])) <= 1
+    nrm = np.linalg.norm(ref.u)
+    assert np.linalg.norm(out["u"] - ref.u) <= 10 * 1e-6 * nrm
+    assert rel(out["C_hom"], ref.C_hom) <= 1e-6
+    assert out["rel_res"][0] <= 2e-6
+    # converged parity on the same workload
+    tight = s.solve(eps, 1e-12, pc)
+    ref_t = osolve.solve(prob, eps, 1e-12, pc)
+    assert np.linalg.norm(tight["u"] - ref_t.u) <= 1e-10 * np.linalg.norm(ref_t.u)
+    assert rel(tight["C_hom"], ref_t.C_hom) <= 1e-9
+    st = tight["stress"][0]
+    assert rel(st, ref_t.stress[0]) <= 1e-9
+
+
+@pytest.mark.parametrize("shape,normal,tangent", [((32, 8), [0, 2], [1]), ((16, 4, 4), [0, 4, 5], [1, 2, 3])])
+def test_laminate_closed_form(shape, normal, tangent):
+    from tests.test_oracle_homogenisation import _laminate_C_hom
+    from paper_2508_02613_gb300.jfft import Solver
+    d = len(shape)
+    rho = laminate_density(shape, 1e2)
+    s = Solver(shape, rho, 0.3)
+    out = s.solve(mandel_unit_loads(d), 1e-13, "green_jacobi")
+    layers = rho.reshape(shape[0], -1)[:, 0]
+    want = _laminate_C_hom([e * fe.C_unit(d, 0.3) for e in layers], normal, tangent)
+    assert rel(out["C_hom"], want) <= 1e-10
+
+
+def test_void_replacement_value_invariance():
+    from paper_2508_02613_gb300.jfft import Solver
+    rho = np.kron(cosine_density((4, 4), float("inf")), np.ones((4, 4)))
+    its = []
+    for rep in (1e-15, 1.0, 1e15):
+        s = Solver(rho.shape, rho, 0.3, void_value=rep, C_ref=fe.C_unit(2, 0.3) * rho.mean())
+        out = s.solve(np.array([[1.0, 1.0, 0.0]]), 1e-8, "green_jacobi")
+        assert out["status"] == 0
+        its.append(int(out["iters"][0]))
+    assert its[0] == its[1] == its[2]
+
+
+def test_batched_loads_equal_single_loads():
+    shape = (64, 64)
+    rho, _ = _problem(shape, 10)
+    s = _solver(shape, rho)
+    eps = mandel_unit_loads(2)
+    batch = s.solve(eps, 1e-8, "green_jacobi")
+    for g in range(3):
+        one = s.solve(eps[g:g + 1], 1e-8, "green_jacobi")
+        assert int(one["iters"][0]) == int(batch["iters"][g])
+        assert np.array_equal(one["u"][0], batch["u"][g])
+        assert np.array_equal(one["C_hom"][:, 0], batch["C_hom"][:, g])
+
+
+def test_deterministic_and_counts_launches():
+    shape = (64, 32)
+    rho, _ = _problem(shape, 11)
+    s = _solver(shape, rho)
+    a = s.solve(mandel_unit_loads(2), 1e-8, "green_jacobi")
+    n0 = s.launch_count
+    b = s.solve(mandel_unit_loads(2), 1e-8, "green_jacobi")
+    assert s.launch_count > n0
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["C_hom"], b["C_hom"])
+    s.set_profiling(True)
+    s.solve(mandel_unit_loads(2)[:1], 1e-8, "green_jacobi")
+    prof = s.profile()
+    assert prof["apply_K"][0] > 0 and prof["fft_lines"][1] > 0
+
+
+def test_device_io_matches_host_io():
+    torch = pytest.importorskip("torch")
+    shape = (32, 64)
+    rho, _ = _problem(shape, 12)
+    s = _solver(shape, rho)
+    eps = mandel_unit_loads(2)
+    host = s.solve(eps, 1e-8, "green")
+    s.set_io_memory("device")
+    dev = s.solve(torch.tensor(eps, device="cuda"), 1e-8, "green")
+    assert np.array_equal(host["u"], dev["u"].cpu().numpy())
+    assert np.array_equal(host["C_hom"], dev["C_hom"].cpu().numpy())
+
+
+def test_argument_errors_are_reported():
+    from paper_2508_02613_gb300.jfft import JfftError, Solver
+    with pytest.raises(JfftError) as ei:
+        Solver((6, 8), np.ones((6, 8)), 0.3)
+    assert ei.value.status == 7 and "power of two" in str(ei.value)
+    bad = np.ones((8, 8))
+    bad[0, 0] = -1.0
+    with pytest.raises(JfftError) as ei:
+        Solver((8, 8), bad, 0.3)
+    assert ei.value.status == 1
+    s = Solver((8, 8), np.ones((8, 8)), 0.3, max_loads=3)
+    with pytest.raises(JfftError):
+        s.solve(np.eye(3).repeat(2, axis=0), 1e-6)
