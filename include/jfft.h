@@ -204,6 +204,36 @@ jfft_status jfft_solve_rhs(jfft_solver* h, int count, const double* f, double to
 jfft_status jfft_postprocess(jfft_solver* h, int count, const double* eps_bar, const double* u,
                              double* stress, double* C_hom);
 
+/*
+ * Allocation-free operator step (the paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, e.g. code inside a framework that
+ * has already reserved the device memory for its own pool, or a latency-critical
+ * loop that must not take the implicit device synchronisation that cudaMalloc or
+ * cudaFree can cause).
+ *
+ * Computes y = K x and xy = x . y for one field with K = B^T W C B, C = E_e
+ * C_unit(nu), on the given grid, without a handle and without allocating: no
+ * cudaMalloc, cudaFree or allocating library call. All pointers are device
+ * pointers on the current device, owned by the caller: E [N] Young's modulus per
+ * voxel, x [d][N] input, y [d][N] output, xy one double (output). stream is a
+ * cudaStream_t or NULL; the call only enqueues work on it and returns.
+ *
+ * Scratch: the per-block partial sums of x . y live in a library-owned static
+ * device array of 8192 doubles (64 KiB), held on every GPU that loads the library
+ * until the process exits. The first call on a device looks up that array's
+ * address with that device current (make this first call before any stream
+ * capture). All calls share the array and each call overwrites the part it uses,
+ * so calls that may overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.
+ *
+ * Errors: JFFT_ERR_ARG for NULL pointers, nu outside (-1, 0.5) or dim not 2/3;
+ * JFFT_ERR_UNSUPPORTED for axis lengths that are not powers of two in 4..2048
+ * (2D) / 4..1024 (3D) or a launch that would need more than 8192 partial sums;
+ * JFFT_ERR_CUDA if a CUDA call fails.
+ */
+jfft_status jfft_apply_K_dot_noalloc(const jfft_grid* grid, double nu, const double* E, const double* x,
+                                     double* y, double* xy, void* stream);
+
 /* ---- instrumentation ---- */
 
 /* Number of kernels this handle has launched since creation. */

@@ -102,6 +102,10 @@ cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, 
                            double* y, int nb, int64_t field_stride, const StrainShift* shifts, double sgn, int dot_mode,
                            double* partial, int* nparts, const CgState* cg, cudaStream_t st);
 
+// S3, one rhs, with a caller-supplied partial buffer of `cap` entries (see operator.cu).
+cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const double* E, const double* x, double* y,
+                                      double* partial, int cap, int* nparts, cudaStream_t st);
+
 // S8: element-averaged Mandel stress [nb][d*][N] (stress may be NULL) and partial
 // sums of vol * stress in partial[(b d* + s) * kMaxPartials + blk].
 cudaError_t launch_stress(const Grid& g, const ElemConst& ec, const double* E, const double* u, int nb,

@@ -244,6 +244,35 @@ cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, 
   return apply_K_d<3>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st);
 }
 
+// The CG operator variant (y = K x with per-CTA partial sums of x.y) for a caller
+// that supplies its own partial-sum buffer with room for `cap` entries: the march
+// segment is lengthened until the CTA count fits (nparts receives that count), or
+// cudaErrorInvalidValue if even a full-length march needs more than `cap`.
+template <int D>
+static cudaError_t apply_K_dot_capped_t(const Grid& g, const ElemConst& ec, const double* E, const double* x,
+                                        double* y, double* partial, int cap, int* nparts, cudaStream_t st) {
+  MarchGeom m = march_geom<D>(g);
+  const int64_t tiles = (int64_t)m.tiles1 * m.tiles2;
+  while (tiles * (g.n[0] / m.seg) > cap && m.seg < g.n[0]) m.seg *= 2;
+  if (tiles * (g.n[0] / m.seg) > cap) return cudaErrorInvalidValue;
+  const size_t smem = march_smem<D>(m);
+  auto kern = k_apply_K<D, 1, true, true, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, 1);
+  const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;
+  JFFT_K("apply_K_dot_capped", st,
+         kern<<<grid, threads, smem, st>>>(g, m, ec, E, 0.0, x, y, 0, nullptr, 1.0, partial, nullptr));
+  *nparts = grid.x * grid.y;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const double* E, const double* x, double* y,
+                                      double* partial, int cap, int* nparts, cudaStream_t st) {
+  if (g.d == 2) return apply_K_dot_capped_t<2>(g, ec, E, x, y, partial, cap, nparts, st);
+  return apply_K_dot_capped_t<3>(g, ec, E, x, y, partial, cap, nparts, st);
+}
+
 // ------------------------------------------------------------------ S8
 template <int D>
 __global__ void __launch_bounds__(256) k_stress(Grid g, ElemConst ec, const double* __restrict__ E,

@@ -77,6 +77,8 @@ _SIGNATURES = {
     "jfft_set_profiling": (c_int, [c_void_p, c_int]),
     "jfft_profile_json": (c_char_p, [c_void_p]),
     "jfft_workspace_bytes": (c_size_t, [c_void_p]),
+    "jfft_apply_K_dot_noalloc": (c_int, [POINTER(JfftGrid), c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_void_p]),
 }
 
 
@@ -125,6 +127,16 @@ def _f64(a, shape=None):
     if shape is not None:
         out = out.reshape(shape)
     return out
+
+
+def apply_K_dot_noalloc(shape, nu, E, x, y, xy, stream=None) -> int:
+    """jfft_apply_K_dot_noalloc on CUDA tensors E [*shape], x / y [d, *shape], xy [1];
+    returns the status code (no allocation happens in the library)."""
+    lib = load()
+    d = len(shape)
+    g = JfftGrid(d, (c_int64 * 3)(*(list(int(s) for s in shape) + [0] * (3 - d))))
+    return lib.jfft_apply_K_dot_noalloc(ctypes.byref(g), float(nu), _ptr(E), _ptr(x), _ptr(y), _ptr(xy),
+                                        c_void_p(stream) if stream else None)
 
 
 class Solver:
