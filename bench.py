@@ -157,6 +157,19 @@ def traffic_bytes_per_unit(kernel, shape, d=2):
     return None
 
 
+def aggregate(ms_local, world, solves_per_step, dist=None, device=None):
+    """Whole-job throughput of N independent replicas: every rank ran the same
+    per-rank workload; the job time is the slowest rank's time (max over ranks, the
+    only collective), value = N x solves per step / that time. Returns (ms, value)."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * solves_per_step / (ms / 1e3)
+
+
 # ----------------------------------------------------------------- CPU side
 def cpu_sample(seconds_budget=25.0):
     """Time the oracle as it stands on a bounded sample of the workload (single process).
@@ -350,13 +363,8 @@ def main():
     prof = s.profile()
     s.set_profiling(False)
     clk = clocks.stop()
-    ms = statistics.mean(times)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     solves_per_step = len(CONTRASTS) * len(PRECONDS) * N_LOADS
-    value = world * solves_per_step / (ms / 1e3)
+    ms, value = aggregate(statistics.mean(times), world, solves_per_step, dist, "cuda")
 
     # ---- e2e through the C ABI with host buffers
     e2e = None
@@ -385,12 +393,9 @@ def main():
         for _ in range(args.steps):
             step_host()
         barrier()
-        t_e2e = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * solves_per_step / t_e2e, "unit": "solves/s",
+        t_e2e_ms, e2e_value = aggregate((time.perf_counter() - t0) / args.steps * 1e3, world, solves_per_step,
+                                        dist, "cuda")
+        e2e = {"value": e2e_value, "unit": "solves/s",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
         sh.close()
 
