@@ -52,6 +52,15 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # SMs x max clock x FP64 flop/clk/
 ITER_COUNTS = os.path.join(ROOT, "oracle", "data", "iters_2d_1024.json")
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this machine (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 # ----------------------------------------------------------------- helpers
 def env_int(name, default):
     try:
@@ -118,6 +127,7 @@ class ClockSampler:
 
 
 def flops_per_unit(kernel, shape, d=2):
+    kernel = kernel[:-4] if kernel.endswith("_f32") else kernel
     """Algorithmic FLOPs of one kernel for one load case (one right-hand side).
 
     FFT passes use the conventional 5 L log2 L per complex transform of length L
@@ -142,19 +152,22 @@ def flops_per_unit(kernel, shape, d=2):
 
 
 def traffic_bytes_per_unit(kernel, shape, d=2):
-    """Compulsory DRAM bytes of one kernel for one load case (FP64)."""
+    """Compulsory DRAM bytes of one kernel for one load case; kernels whose name ends in
+    _f32 move FP32 data (s = 4 bytes per real), the others FP64 (s = 8)."""
+    s = 4 if kernel.endswith("_f32") else 8
+    k = kernel[:-4] if kernel.endswith("_f32") else kernel
     n0, n1 = shape
     N = n0 * n1
     F = n0 * (n1 // 2 + 1)
-    if kernel == "fft_lines":
-        return 2 * d * F * 16 + F * 3 * 8                          # spectrum in+out, symbol table
-    if kernel == "fft_rows_real_fwd":
-        return d * N * 8 + d * F * 16 + N * 8
-    if kernel == "fft_cols_real_inv":
-        return d * F * 16 + 2 * d * N * 8 + N * 8
-    if kernel == "apply_K":
-        return 2 * d * N * 8 + N * 8
-    return None
+    table = {
+        "fft_lines": 2 * d * F * 2 * s + F * 3 * s,              # spectrum in + out, symbol table
+        "fft_rows_real_fwd": d * N * s + d * F * 2 * s + N * s,   # r, spectrum, J^1/2 scale
+        "fft_cols_real_inv": d * F * 2 * s + 2 * d * N * s + N * s,   # spectrum, z, r (dot), scale
+        "apply_K": 2 * d * N * s + N * s,                         # p, q, E
+        "cg_xr": 6 * d * N * s,                                   # x, r read+write, p, q
+        "cg_p": 3 * d * N * s,                                    # p read+write, z
+    }
+    return table.get(k)
 
 
 def aggregate(ms_local, world, solves_per_step, dist=None, device=None):
@@ -319,9 +332,10 @@ def main():
     rho_d = torch.tensor(rho_h, device="cuda")
     eps_h = np.eye(3)
     eps_d = torch.tensor(eps_h, device="cuda")
-    s = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
-               stream=stream.cuda_stream, io="device", max_loads=N_LOADS)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    uuid = str(getattr(torch.cuda.get_device_properties(local), "uuid", ""))
+    smi_id = ("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or local)
+    solves_per_step = len(CONTRASTS) * len(PRECONDS) * N_LOADS
 
     def barrier():
         torch.cuda.synchronize()
@@ -329,44 +343,91 @@ def main():
             dist.barrier()
             torch.cuda.synchronize()
 
-    def step(record=None):
-        for c in CONTRASTS:
-            s.set_material(rho_d, e_min=1.0 / c)
-            for pc in PRECONDS:
-                out = s.solve(eps_d, TOL, pc, want_stress=False)
-                if record is not None:
-                    record[(c, pc)] = [int(v) for v in out["iters"].cpu().tolist()]
+    def run_leg(precision):
+        """Warm-up, one recording pass (iterations, time to tolerance per solve call),
+        then the timed steps with per-kernel CUDA events and clock sampling."""
+        s = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
+                   stream=stream.cuda_stream, io="device", max_loads=N_LOADS, precision=precision)
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
+        def step(record=None):
+            for c in CONTRASTS:
+                s.set_material(rho_d, e_min=1.0 / c)
+                for pc in PRECONDS:
+                    if record is not None:
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                    out = s.solve(eps_d, TOL, pc, want_stress=False)
+                    if record is not None:
+                        e1.record(stream)
+                        e1.synchronize()
+                        record[(c, pc)] = {"iters": [int(v) for v in out["iters"].cpu().tolist()],
+                                           "refine": [int(v) for v in out["refine_steps"].cpu().tolist()],
+                                           "rel_res": [float(v) for v in out["rel_res"].cpu().tolist()],
+                                           "ms": e0.elapsed_time(e1)}
 
-    iters = {}
-    step(iters)            # untimed pass that records iteration counts
-    barrier()
-    uuid = str(getattr(torch.cuda.get_device_properties(local), "uuid", ""))
-    clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or local))
-    clocks.start()
-    s.set_profiling(True)
-    n_launch0 = s.launch_count
-    times = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)   # L2 flush (256 MiB > 129 MB L2), outside the timed interval
+        for _ in range(args.warmup):
+            step()
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
+        rec = {}
+        step(rec)
         barrier()
-        times.append(e0.elapsed_time(e1))
-    launches = s.launch_count - n_launch0
-    prof = s.profile()
-    s.set_profiling(False)
-    clk = clocks.stop()
-    solves_per_step = len(CONTRASTS) * len(PRECONDS) * N_LOADS
-    ms, value = aggregate(statistics.mean(times), world, solves_per_step, dist, "cuda")
+        clocks = ClockSampler(smi_id)
+        clocks.start()
+        s.set_profiling(True)
+        n0 = s.launch_count
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)   # L2 flush (256 MiB > 129 MB L2), outside the timed interval
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            barrier()
+            times.append(e0.elapsed_time(e1))
+        launches = s.launch_count - n0
+        prof = s.profile()
+        s.set_profiling(False)
+        clk = clocks.stop()
+        s.close()
+        ms, value = aggregate(statistics.mean(times), world, solves_per_step, dist, "cuda")
+        return {"ms": ms, "value": value, "times": times, "rec": rec, "prof": prof, "launches": launches,
+                "clocks": clk}
 
-    # ---- e2e through the C ABI with host buffers
+    def roofline(leg, alu):
+        """Dominant kernel of the timed region with its achieved rate. Units are right-hand-
+        side applications: per load, one operator and one preconditioner per PCG iteration."""
+        n_units = sum(sum(r["iters"]) for r in leg["rec"].values()) * args.steps
+        rows = sorted(((k, v[0], v[1]) for k, v in leg["prof"].items()), key=lambda r: -r[2])
+        total_ms = sum(r[2] for r in rows)
+        peak_gbs, peak_kind = hbm_peak_gbs()
+        for name, nl, tot in rows:
+            byt = traffic_bytes_per_unit(name, SHAPE)
+            fl = flops_per_unit(name, SHAPE)
+            if byt is None or fl is None:
+                continue
+            out = {"kernel": name, "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
+                   "traffic": None, "algorithmic_bytes_per_unit": byt, "units": n_units}
+            gbs = n_units * byt / (tot / 1e3) / 1e9
+            tfl = n_units * fl / (tot / 1e3) / 1e12
+            if alu:
+                out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tfl / FP64_PEAK_TFLOPS, "hbm_GBps_algorithmic": gbs,
+                            "peak_note": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (probe: 1.197 TFLOP/s DFMA)"})
+            else:
+                out.update({"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
+                            "peak_note": f"HBM copy bandwidth, {peak_kind} (burst)"})
+            return out
+        return None
+
+    fp64 = run_leg("fp64")
+    mixed = run_leg("mixed")
+    ms, value, launches = fp64["ms"], fp64["value"], fp64["launches"]
+    iters = {k: v["iters"] for k, v in fp64["rec"].items()}
+    prof = fp64["prof"]
+    roof = roofline(fp64, alu=True)
+
+    # ---- e2e through the C ABI with host buffers (FP64, the value's configuration)
     e2e = None
     if not args.no_e2e:
         sh = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
@@ -399,27 +460,18 @@ def main():
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
         sh.close()
 
-    # ---- roofline of the dominant kernel (CUDA events around each launch, timed region)
-    units = {}  # right-hand-side applications per kernel over the timed region
-    n_pc = sum(sum(v) for v in iters.values())  # preconditioner and CG-operator applications per step
-    units["fft_lines"] = units["fft_rows_real_fwd"] = units["fft_cols_real_inv"] = units["apply_K"] = \
-        n_pc * args.steps
-    roof = None
-    rows = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda r: -r[2])
-    total_ms = sum(r[2] for r in rows)
-    for name, nl, tot in rows:
-        fl = flops_per_unit(name, SHAPE)
-        if fl is None:
-            continue
-        achieved = units[name] * fl / (tot / 1e3) / 1e12
-        byt = traffic_bytes_per_unit(name, SHAPE)
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
-                "algorithmic_bytes_per_unit": byt,
-                "hbm_GBps_algorithmic": units[name] * byt / (tot / 1e3) / 1e9,
-                "peak_note": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (probe measured 1.197 TFLOP/s DFMA)"}
-        break
+    mixed_line = {
+        "value": mixed["value"], "unit": "solves/s", "ms_per_step": mixed["ms"], "speedup_vs_fp64": fp64["ms"] / mixed["ms"],
+        "dtype": "f32 inner PCG (operator, FFT, preconditioner, vectors) + f64 scalars, residual and solution",
+        "roofline": roofline(mixed, alu=False), "clocks": mixed["clocks"], "gpu_launches": mixed["launches"] // args.steps,
+        "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in mixed["rec"].items()},
+        "iters": {f"{pc}@{c:g}": v["iters"] for (c, pc), v in mixed["rec"].items()},
+        "refine_steps": {f"{pc}@{c:g}": v["refine"] for (c, pc), v in mixed["rec"].items()},
+        "rel_res_max": max(max(v["rel_res"]) for v in mixed["rec"].values()),
+        "kernels_ms_total": {k: round(v[1], 3) for k, v in mixed["prof"].items()},
+    }
+    clk = fp64["clocks"]
+    times = fp64["times"]
 
     cpu_line = None
     if cpu is not None:
@@ -440,14 +492,15 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written before each timed step (outside the timed interval)"},
             "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": launches // args.steps,
-            "clocks": clk,
+            "clocks": clk, "mixed": mixed_line,
             "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
+                       "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in fp64["rec"].items()},
+                       "rel_res_max": max(max(v["rel_res"]) for v in fp64["rec"].values()),
                        "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()},
                        "kernel_launches": {k: v[0] for k, v in prof.items()},
                        "step_ms": times},
         }
         print(json.dumps(line), flush=True)
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

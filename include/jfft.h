@@ -70,7 +70,12 @@ typedef enum {
   JFFT_MAT_DENSITY = 1       /* field = rho per voxel; E = e_min + (e_max - e_min) rho^exponent, on the device */
 } jfft_material_kind;
 
-typedef enum { JFFT_PREC_FP64 = 0 } jfft_precision;
+typedef enum {
+  JFFT_PREC_FP64 = 0,        /* every step in FP64 */
+  JFFT_PREC_MIXED = 1        /* FP64 iterative refinement around an FP32 PCG: operator, FFT, preconditioner and
+                                vectors of the inner solve in FP32, CG scalars and every reduction above the
+                                thread in FP64, residual f - K u and the solution u in FP64 */
+} jfft_precision;
 
 typedef enum {
   JFFT_STOP_REL = 0,         /* ||r_k||_2 <= tol ||f||_2 (r the recursively updated residual) */
@@ -108,14 +113,18 @@ typedef struct {
   int max_loads;             /* largest n_loads / count accepted by later calls (default 6) */
   double void_value;         /* replaces zero diagonal entries of K before J = diag^-1 (default 1, Sec. 3.2) */
   int device;                /* CUDA device ordinal (default 0) */
+  double inner_tol;          /* MIXED: relative residual of each FP32 inner solve (default 1e-3) */
+  int max_refine;            /* MIXED: largest number of inner solves per load (default 30) */
 } jfft_options;
 
 typedef struct {
   double* u;                 /* [n_loads][d][N] zero-mean fluctuation displacement, or NULL */
   double* stress;            /* [n_loads][d*][N] element-averaged Mandel stress, or NULL */
   double* C_hom;             /* [d*][n_loads]: column g = cell-averaged stress for eps_bar[g], or NULL */
-  int* iters;                /* [n_loads] PCG iterations (operator applications in the loop), or NULL */
+  int* iters;                /* [n_loads] PCG iterations (operator applications in the loop; MIXED: summed
+                                over the inner solves), or NULL */
   double* rel_res;           /* [n_loads] true ||f - K u||_2 / ||f||_2 recomputed at exit (0 if f = 0), or NULL */
+  int* refine_steps;         /* [n_loads] MIXED: FP32 inner solves run (FP64: 1), or NULL */
 } jfft_result;
 
 /* Fill *opt with the defaults listed above. */
@@ -172,7 +181,9 @@ jfft_status jfft_get_material(jfft_solver* h, double* E);
 /* S2: f = -B^T W C eps_bar for count strains [count][d*] -> f [count][d][N] (Eq. lin_system_exp). */
 jfft_status jfft_rhs(jfft_solver* h, int count, const double* eps_bar, double* f);
 
-/* S3: y = K x for count fields [count][d][N], K = B^T W C B matrix free (Sec. 3.1 "Matrix-free assembly"). */
+/* S3: y = K x for count fields [count][d][N], K = B^T W C B matrix free (Sec. 3.1 "Matrix-free assembly").
+ * With JFFT_PREC_MIXED this and jfft_apply_precond run the FP32 kernels of the
+ * inner solve (inputs rounded to FP32, outputs widened to FP64). */
 jfft_status jfft_apply_K(jfft_solver* h, int count, const double* x, double* y);
 
 /* S5: diag(K) [d][N] before the void rule, by the closed form or by Alg. 2. */
@@ -194,7 +205,8 @@ jfft_status jfft_apply_precond(jfft_solver* h, int precond, int count, const dou
 /*
  * S4 + S7: PCG for count arbitrary right-hand sides f [count][d][N] from u_0 = 0.
  * u [count][d][N] receives the raw iterate (no mean removal), iters [count] the
- * iteration counts. With tol = 0 exactly max_iter iterations run (same-k tests).
+ * iteration counts. With tol = 0 exactly max_iter iterations run (same-k tests,
+ * FP64 handles). With JFFT_PREC_MIXED the result is the refined FP64 solution.
  */
 jfft_status jfft_solve_rhs(jfft_solver* h, int count, const double* f, double tol, int precond,
                            double* u, int* iters);

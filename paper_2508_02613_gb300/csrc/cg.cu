@@ -3,29 +3,33 @@
 // Scalars never leave the device during the iteration: each stage kernel reduces
 // the per-block partials of one right-hand side in a fixed order and updates its
 // CgState; the vector kernels read alpha / beta from there and skip right-hand
-// sides that are done.
+// sides that are done. Vector kernels are templated on the working precision T;
+// the scalars and every reduction above the thread level stay in FP64.
 #include "jfft_internal.cuh"
 #include "reduce.cuh"
 
 namespace jfft {
 
-static int vec_blocks(int64_t n2) {  // n2 = number of double2 elements per rhs
+static int vec_blocks(int64_t n2) {  // n2 = number of 2-vectors per rhs
   return (int)std::max<int64_t>(1, std::min<int64_t>((n2 + 255) / 256, 152 * 4));
 }
 
+template <typename T> static const char* nm(const char* d64, const char* d32) { return sizeof(T) == 8 ? d64 : d32; }
+
 // x += alpha p ; r -= alpha q ; partial ||r||^2
-__global__ void __launch_bounds__(256) k_cg_xr(double2* __restrict__ x, double2* __restrict__ r,
-                                               const double2* __restrict__ p, const double2* __restrict__ q,
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_xr(cplx<T>* __restrict__ x, cplx<T>* __restrict__ r,
+                                               const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ q,
                                                int64_t n2, int64_t stride2, const CgState* __restrict__ cg,
                                                double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (cg[b].done) return;
-  const double al = cg[b].alpha;
+  const T al = (T)cg[b].alpha;
   const int64_t off = (int64_t)b * stride2;
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 xv = x[off + i], rv = r[off + i];
-    const double2 pv = p[off + i], qv = q[off + i];
+    cplx<T> xv = x[off + i], rv = r[off + i];
+    const cplx<T> pv = p[off + i], qv = q[off + i];
     xv.x = fma(al, pv.x, xv.x);
     xv.y = fma(al, pv.y, xv.y);
     rv.x = fma(-al, qv.x, rv.x);
@@ -35,66 +39,78 @@ __global__ void __launch_bounds__(256) k_cg_xr(double2* __restrict__ x, double2*
     acc = fma(rv.x, rv.x, acc);
     acc = fma(rv.y, rv.y, acc);
   }
-  const double s = block_sum(acc);
+  const double s = block_sum((double)acc);
   if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
 }
 
-cudaError_t launch_cg_xr(const Grid& g, double* x, double* r, const double* p, const double* q, int nb, int64_t stride,
-                         CgState* cg, double* partial, int* nparts, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_cg_xr(const Grid& g, T* x, T* r, const T* p, const T* q, int nb, int64_t stride, CgState* cg,
+                         double* partial, int* nparts, cudaStream_t st) {
   const int64_t n2 = g.d * g.N / 2;
   const int bl = vec_blocks(n2);
-  JFFT_K("cg_xr", st, k_cg_xr<<<dim3(bl, nb), 256, 0, st>>>((double2*)x, (double2*)r, (const double2*)p, (const double2*)q, n2, stride / 2,
-                                       cg, partial));
+  JFFT_K(nm<T>("cg_xr", "cg_xr_f32"), st,
+         k_cg_xr<T><<<dim3(bl, nb), 256, 0, st>>>((cplx<T>*)x, (cplx<T>*)r, (const cplx<T>*)p, (const cplx<T>*)q, n2,
+                                                  stride / 2, cg, partial));
   *nparts = bl;
   return cudaGetLastError();
 }
+template cudaError_t launch_cg_xr<double>(const Grid&, double*, double*, const double*, const double*, int, int64_t,
+                                          CgState*, double*, int*, cudaStream_t);
+template cudaError_t launch_cg_xr<float>(const Grid&, float*, float*, const float*, const float*, int, int64_t,
+                                         CgState*, double*, int*, cudaStream_t);
 
 // p = z + beta p
-__global__ void __launch_bounds__(256) k_cg_p(double2* __restrict__ p, const double2* __restrict__ z, int64_t n2,
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_p(cplx<T>* __restrict__ p, const cplx<T>* __restrict__ z, int64_t n2,
                                               int64_t stride2, const CgState* __restrict__ cg) {
   const int b = blockIdx.y;
   if (cg[b].done) return;
-  const double be = cg[b].beta;
+  const T be = (T)cg[b].beta;
   const int64_t off = (int64_t)b * stride2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 pv = p[off + i];
-    const double2 zv = z[off + i];
+    cplx<T> pv = p[off + i];
+    const cplx<T> zv = z[off + i];
     pv.x = fma(be, pv.x, zv.x);
     pv.y = fma(be, pv.y, zv.y);
     p[off + i] = pv;
   }
 }
 
-cudaError_t launch_cg_p(const Grid& g, double* p, const double* z, int nb, int64_t stride, CgState* cg, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_cg_p(const Grid& g, T* p, const T* z, int nb, int64_t stride, CgState* cg, cudaStream_t st) {
   const int64_t n2 = g.d * g.N / 2;
-  JFFT_K("cg_p", st, k_cg_p<<<dim3(vec_blocks(n2), nb), 256, 0, st>>>((double2*)p, (const double2*)z, n2, stride / 2, cg));
+  JFFT_K(nm<T>("cg_p", "cg_p_f32"), st,
+         k_cg_p<T><<<dim3(vec_blocks(n2), nb), 256, 0, st>>>((cplx<T>*)p, (const cplx<T>*)z, n2, stride / 2, cg));
   return cudaGetLastError();
 }
+template cudaError_t launch_cg_p<double>(const Grid&, double*, const double*, int, int64_t, CgState*, cudaStream_t);
+template cudaError_t launch_cg_p<float>(const Grid&, float*, const float*, int, int64_t, CgState*, cudaStream_t);
 
 // z = J r (J = (J^1/2)^2 per component; identity: z = r), partial r.z
-__global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const double* __restrict__ r, double* __restrict__ z,
-                                                   int64_t stride, const double* __restrict__ js, double3 jscale,
-                                                   double void_js, int identity, const CgState* __restrict__ cg,
+template <typename T>
+__global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__ r, T* __restrict__ z, int64_t stride,
+                                                   const T* __restrict__ js, double3 jscale, double void_js,
+                                                   int identity, const CgState* __restrict__ cg,
                                                    double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (cg && cg[b].done) return;
   const int64_t off = (int64_t)b * stride;
   const int64_t n = g.d * g.N;
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double rv = r[off + i];
-    double zv = rv;
+    const T rv = r[off + i];
+    T zv = rv;
     if (!identity) {
       const int a = (int)(i / g.N);
-      const double s = js[i - a * g.N];
-      const double ka = a == 0 ? jscale.x : (a == 1 ? jscale.y : jscale.z);
-      const double jh = s > 0.0 ? s * ka : void_js;
+      const T s = js[i - a * g.N];
+      const T ka = (T)(a == 0 ? jscale.x : (a == 1 ? jscale.y : jscale.z));
+      const T jh = s > T(0) ? s * ka : (T)void_js;
       zv = jh * jh * rv;
     }
     z[off + i] = zv;
     acc = fma(rv, zv, acc);
   }
-  const double s = block_sum(acc);
+  const double s = block_sum((double)acc);
   if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
 }
 
@@ -102,31 +118,51 @@ cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int
                                   const double* jscale, double void_js, bool identity, double* partial, int* nparts,
                                   const CgState* done, cudaStream_t st) {
   const int bl = vec_blocks(g.d * g.N / 2);
-  JFFT_K("jacobi_pc", st, k_jacobi_pc<<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js, make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                           identity ? 1 : 0, done, partial));
+  JFFT_K("jacobi_pc", st,
+         k_jacobi_pc<double><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
+                                                           make_double3(jscale[0], jscale[1], jscale[2]), void_js,
+                                                           identity ? 1 : 0, done, partial));
+  *nparts = bl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
+                                      const double* jscale, double void_js, bool identity, double* partial,
+                                      int* nparts, const CgState* done, cudaStream_t st) {
+  const int bl = vec_blocks(g.d * g.N / 2);
+  JFFT_K("jacobi_pc_f32", st,
+         k_jacobi_pc<float><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
+                                                          make_double3(jscale[0], jscale[1], jscale[2]), void_js,
+                                                          identity ? 1 : 0, done, partial));
   *nparts = bl;
   return cudaGetLastError();
 }
 
 // partial[b][blk] = sum a_b . c_b
-__global__ void __launch_bounds__(256) k_dot(const double* __restrict__ a, const double* __restrict__ c, int64_t n,
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot(const T* __restrict__ a, const T* __restrict__ c, int64_t n,
                                              int64_t stride, double* __restrict__ partial) {
   const int b = blockIdx.y;
   const int64_t off = (int64_t)b * stride;
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     acc = fma(a[off + i], c[off + i], acc);
-  const double s = block_sum(acc);
+  const double s = block_sum((double)acc);
   if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
 }
 
-cudaError_t launch_dot(const Grid& g, const double* a, const double* c, int nb, int64_t stride, double* partial,
-                       int* nparts, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_dot(const Grid& g, const T* a, const T* c, int nb, int64_t stride, double* partial, int* nparts,
+                       cudaStream_t st) {
   const int bl = vec_blocks(g.d * g.N / 2);
-  JFFT_K("dot", st, k_dot<<<dim3(bl, nb), 256, 0, st>>>(a, c, g.d * g.N, stride, partial));
+  JFFT_K(nm<T>("dot", "dot_f32"), st, k_dot<T><<<dim3(bl, nb), 256, 0, st>>>(a, c, g.d * g.N, stride, partial));
   *nparts = bl;
   return cudaGetLastError();
 }
+template cudaError_t launch_dot<double>(const Grid&, const double*, const double*, int, int64_t, double*, int*,
+                                        cudaStream_t);
+template cudaError_t launch_dot<float>(const Grid&, const float*, const float*, int, int64_t, double*, int*,
+                                       cudaStream_t);
 
 // Scalar stages; one block per rhs.
 __global__ void __launch_bounds__(1024) k_scalars(int stage, CgState* __restrict__ cg, const double* __restrict__ partial,
@@ -203,28 +239,28 @@ cudaError_t launch_reduce_partials(const double* partial, int nparts, int rows, 
   return cudaGetLastError();
 }
 
-// partial[(b d + a)][blk] = sum of field a of rhs b
-__global__ void __launch_bounds__(256) k_field_sums(const double* __restrict__ x, int64_t N, double* __restrict__ partial) {
+// partial[row][blk] = sum of row `row` of x viewed as [rows][n]
+__global__ void __launch_bounds__(256) k_row_sums(const double* __restrict__ x, int64_t n, double* __restrict__ partial) {
   const int row = blockIdx.y;
-  const double* xr = x + (int64_t)row * N;
+  const double* xr = x + (int64_t)row * n;
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) acc += xr[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += xr[i];
   const double s = block_sum(acc);
   if (threadIdx.x == 0) partial[(int64_t)row * kMaxPartials + blockIdx.x] = s;
 }
 
 cudaError_t launch_row_sums(const double* x, int rows, int64_t n, double* partial, int* nparts, cudaStream_t st) {
   const int bl = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 2));
-  JFFT_K("row_sums", st, k_field_sums<<<dim3(bl, rows), 256, 0, st>>>(x, n, partial));
+  JFFT_K("row_sums", st, k_row_sums<<<dim3(bl, rows), 256, 0, st>>>(x, n, partial));
   *nparts = bl;
   return cudaGetLastError();
 }
 
-__global__ void k_sub_mean(double* __restrict__ x, int64_t N, const double* __restrict__ sums) {
+__global__ void k_sub_mean(double* __restrict__ x, int64_t n, const double* __restrict__ sums) {
   const int row = blockIdx.y;
-  const double m = sums[row] / (double)N;
-  double* xr = x + (int64_t)row * N;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) xr[i] -= m;
+  const double m = sums[row] / (double)n;
+  double* xr = x + (int64_t)row * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) xr[i] -= m;
 }
 
 cudaError_t launch_sub_mean(double* x, int rows, int64_t n, const double* sums, cudaStream_t st) {
@@ -240,6 +276,56 @@ __global__ void k_fill(double* x, int64_t n, double v) {
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t st) {
   const int bl = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
   JFFT_K("fill", st, k_fill<<<bl, 256, 0, st>>>(x, n, v));
+  return cudaGetLastError();
+}
+
+// dst[b][i] = active[b] ? (float) src[b][i] : 0
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n, const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  const bool on = active == nullptr || active[b] != 0;
+  const int64_t off = (int64_t)b * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[off + i] = on ? (float)src[off + i] : 0.f;
+}
+
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n_per_rhs, int nb, const int* active, cudaStream_t st) {
+  const int bl = (int)std::max<int64_t>(1, std::min<int64_t>((n_per_rhs + 255) / 256, 152 * 8));
+  JFFT_K("to_f32", st, k_to_f32<<<dim3(bl, nb), 256, 0, st>>>(src, dst, n_per_rhs, active));
+  return cudaGetLastError();
+}
+
+// u += (double) d
+__global__ void k_add_f32(double* __restrict__ u, const float* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += (double)d[i];
+}
+
+cudaError_t launch_add_f32(double* u, const float* d, int64_t n, cudaStream_t st) {
+  const int bl = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  JFFT_K("add_f32", st, k_add_f32<<<bl, 256, 0, st>>>(u, d, n));
+  return cudaGetLastError();
+}
+
+// r = f - q ; partial[b][blk] = sum r.r
+__global__ void __launch_bounds__(256) k_sub_norm(const double* __restrict__ f, const double* __restrict__ q,
+                                                  double* __restrict__ r, int64_t n, double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  const int64_t off = (int64_t)b * n;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = f[off + i] - q[off + i];
+    r[off + i] = v;
+    acc = fma(v, v, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
+}
+
+cudaError_t launch_sub_norm(const Grid& g, const double* f, const double* q, double* r, int nb, double* partial,
+                            int* nparts, cudaStream_t st) {
+  const int bl = vec_blocks(g.d * g.N / 2);
+  JFFT_K("sub_norm", st, k_sub_norm<<<dim3(bl, nb), 256, 0, st>>>(f, q, r, g.d * g.N, partial));
+  *nparts = bl;
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ template <int D> JFFT_HD constexpr int popc(int m) {
 }
 
 // Mode forces F[a][m] (zeroed on entry) from modes W[a][m] for unit E.
-template <int D, typename V> JFFT_HD void mode_forces(const ElemConst& ec, const V (*W)[1 << D], V (*F)[1 << D]) {
+template <int D, typename V> JFFT_HD void mode_forces(const ElemConstT<V>& ec, const V (*W)[1 << D], V (*F)[1 << D]) {
   constexpr int NC = 1 << D;
 #pragma unroll
   for (int mu = 0; mu < NC; ++mu) {
@@ -97,7 +97,7 @@ template <int D, typename V> JFFT_HD void mode_forces(const ElemConst& ec, const
 // Corner forces f[a][c] = E * K_e-unit u, with u[a][c] corner displacements and an
 // optional macroscopic strain shift added to the single-axis modes.
 template <int D, typename V, bool SHIFT>
-JFFT_HD void element_force(const ElemConst& ec, const StrainShift* sh, V (*u)[1 << D], V E) {
+JFFT_HD void element_force(const ElemConstT<V>& ec, const StrainShift* sh, V (*u)[1 << D], V E) {
   constexpr int NC = 1 << D;
   V F[D][NC];
 #pragma unroll

@@ -38,6 +38,14 @@ struct jfft_solver {
   double *partial = nullptr, *red = nullptr;
   CgState* cg = nullptr;
   StrainShift* shifts = nullptr;
+  // FP32 copies and vectors of the mixed-precision inner solve
+  int precision = JFFT_PREC_FP64;
+  float *E32 = nullptr, *js32 = nullptr, *G32 = nullptr;
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  float2 *T32 = nullptr, *U32 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *z32 = nullptr;
+  int* active = nullptr;
+  int* active_h = nullptr;
   std::vector<void*> allocs;
   // pinned host mirrors
   CgState* cg_h = nullptr;
@@ -163,6 +171,8 @@ extern "C" void jfft_default_options(jfft_options* o) {
   o->max_loads = 6;
   o->void_value = 1.0;
   o->device = 0;
+  o->inner_tol = 1e-3;
+  o->max_refine = 30;
 }
 
 static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
@@ -180,8 +190,10 @@ static void free_all(jfft_solver* h) {
   h->allocs.clear();
   if (h->cg_h) cudaFreeHost(h->cg_h);
   if (h->red_h) cudaFreeHost(h->red_h);
+  if (h->active_h) cudaFreeHost(h->active_h);
   h->cg_h = nullptr;
   h->red_h = nullptr;
+  h->active_h = nullptr;
   for (auto& pe : h->pend) { h->pool.push_back(pe.a); h->pool.push_back(pe.b); }
   for (auto ev : h->pool) cudaEventDestroy(ev);
   h->pool.clear();
@@ -260,6 +272,14 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   h->ec_ref = make_elem_const(g.d, hh, lam, mu);
   s = build_symbol(h);
   if (s) return s;
+  if (h->precision == JFFT_PREC_MIXED) {
+    CK(launch_to_f32(h->E, h->E32, g.N, 1, nullptr, h->st));
+    CK(launch_to_f32(h->js, h->js32, g.N, 1, nullptr, h->st));
+    CK(launch_to_f32(h->G, h->G32, g.F * h->ds, 1, nullptr, h->st));
+    for (int a = 0; a < g.d; ++a)
+      CK(launch_to_f32(reinterpret_cast<const double*>(h->tw[a]), reinterpret_cast<float*>(h->tw32[a]), 2 * g.n[a], 1,
+                       nullptr, h->st));
+  }
   return sync(h);
 }
 
@@ -297,7 +317,13 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   g.M = g.n[d - 1] / 2;
   g.F = g.N / g.n[d - 1] * (g.M + 1);
   h->ds = d * (d + 1) / 2;
-  if (o.precision != JFFT_PREC_FP64) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "only FP64 precision is built"));
+  if (o.precision != JFFT_PREC_FP64 && o.precision != JFFT_PREC_MIXED)
+    return bail(fail(h, JFFT_ERR_ARG, "unknown precision"));
+  if (o.precision == JFFT_PREC_MIXED) {
+    if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return bail(fail(h, JFFT_ERR_ARG, "inner_tol must lie in (0, 1)"));
+    if (o.max_refine <= 0) return bail(fail(h, JFFT_ERR_ARG, "max_refine must be positive"));
+  }
+  h->precision = o.precision;
   if (o.max_iter <= 0) return bail(fail(h, JFFT_ERR_ARG, "max_iter must be positive"));
   if (o.stop_mode != JFFT_STOP_REL && o.stop_mode != JFFT_STOP_ABS_SQ) return bail(fail(h, JFFT_ERR_ARG, "bad stop_mode"));
   if (o.check_every <= 0) o.check_every = 8;
@@ -374,7 +400,13 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   total += 5 * (size_t)nbmax * fe * sizeof(double);                 // x r p q z
   const size_t part_rows = (size_t)nbmax * 6;
   total += part_rows * kMaxPartials * sizeof(double);
-  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift));
+  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int));
+  if (o.precision == JFFT_PREC_MIXED) {
+    total += 2 * g.N * sizeof(float) + (size_t)g.F * h->ds * sizeof(float);
+    for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
+    total += (size_t)spec_n * sizeof(float2) * (d == 3 ? 2 : 1);
+    total += 5 * (size_t)nbmax * fe * sizeof(float);
+  }
   if (o.hbm_budget && total > o.hbm_budget) {
     char msg[160];
     snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds hbm_budget %zu", total, o.hbm_budget);
@@ -403,10 +435,26 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->red, 1024 * sizeof(double));
   AL(h->cg, nbmax * sizeof(CgState));
   AL(h->shifts, nbmax * sizeof(StrainShift));
+  AL(h->active, nbmax * sizeof(int));
+  if (o.precision == JFFT_PREC_MIXED) {
+    AL(h->E32, g.N * sizeof(float));
+    AL(h->js32, g.N * sizeof(float));
+    AL(h->G32, (size_t)g.F * h->ds * sizeof(float));
+    for (int a = 0; a < d; ++a) AL(h->tw32[a], (size_t)g.n[a] * sizeof(float2));
+    AL(h->T32, (size_t)spec_n * sizeof(float2));
+    if (d == 3) AL(h->U32, (size_t)spec_n * sizeof(float2));
+    AL(h->x32, (size_t)nbmax * fe * sizeof(float));
+    AL(h->r32, (size_t)nbmax * fe * sizeof(float));
+    AL(h->p32, (size_t)nbmax * fe * sizeof(float));
+    AL(h->q32, (size_t)nbmax * fe * sizeof(float));
+    AL(h->z32, (size_t)nbmax * fe * sizeof(float));
+  }
 #undef AL
   ce = cudaMallocHost((void**)&h->cg_h, nbmax * sizeof(CgState));
   if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
   ce = cudaMallocHost((void**)&h->red_h, 1024 * sizeof(double));
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
+  ce = cudaMallocHost((void**)&h->active_h, nbmax * sizeof(int));
   if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
 
   for (int a = 0; a < d; ++a) {
@@ -467,44 +515,79 @@ static bool valid_pc(int pc) {
   return pc == JFFT_PC_NONE || pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI || pc == JFFT_PC_JACOBI;
 }
 
+// Buffers of one working precision.
+template <typename T> struct Work {
+  T *x, *r, *p, *q, *z;
+  const T* E;
+  const T* js;
+  FftPlanT<T> pl;
+};
+
+static Work<double> work64(jfft_solver* h) {
+  return {h->x, h->r, h->p, h->q, h->z, h->E, h->js, {{h->tw[0], h->tw[1], h->tw[2]}, h->T, h->U, h->G}};
+}
+static Work<float> work32(jfft_solver* h) {
+  return {h->x32, h->r32, h->p32, h->q32, h->z32, h->E32, h->js32, {{h->tw32[0], h->tw32[1], h->tw32[2]}, h->T32,
+                                                                    h->U32, h->G32}};
+}
+
+static cudaError_t apply_op(jfft_solver* h, const Work<double>& w, const double* x, double* y, int nb, int dot, int* np,
+                            const CgState* cg) {
+  return launch_apply_K(h->g, h->ec, w.E, 0.0, x, y, nb, field_elems(h), nullptr, 1.0, dot, h->partial, np, cg, h->st);
+}
+static cudaError_t apply_op(jfft_solver* h, const Work<float>& w, const float* x, float* y, int nb, int dot, int* np,
+                            const CgState* cg) {
+  return launch_apply_K_f32(h->g, h->ec, w.E, x, y, nb, field_elems(h), dot, h->partial, np, cg, h->st);
+}
+
+static cudaError_t precond_op(jfft_solver* h, const Work<double>& w, int pc, const double* r, double* z, int nb,
+                              const CgState* cg, int* np) {
+  if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
+    return launch_green_precond(h->g, w.pl, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js,
+                                pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st);
+  return launch_jacobi_precond(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
+                               h->partial, np, cg, h->st);
+}
+static cudaError_t precond_op(jfft_solver* h, const Work<float>& w, int pc, const float* r, float* z, int nb,
+                              const CgState* cg, int* np) {
+  if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
+    return launch_green_precond_f32(h->g, w.pl, r, z, nb, w.js, h->jscale, h->void_js, pc == JFFT_PC_GREEN_JACOBI,
+                                    h->partial, np, cg, h->st);
+  return launch_jacobi_precond_f32(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
+                                   h->partial, np, cg, h->st);
+}
+
 static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, int nb, const CgState* cg, int* np) {
-  const Grid& g = h->g;
-  if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI) {
-    FftPlan pl = {{h->tw[0], h->tw[1], h->tw[2]}, h->T, h->U, h->G};
-    CK(launch_green_precond(g, pl, r, z, nb, field_elems(h), h->js, h->jscale, h->void_js,
-                            pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st));
-  } else {
-    CK(launch_jacobi_precond(g, r, z, nb, field_elems(h), h->js, h->jscale, h->void_js, pc == JFFT_PC_NONE, h->partial,
-                             np, cg, h->st));
-  }
+  CK(precond_op(h, work64(h), pc, r, z, nb, cg, np));
   return JFFT_OK;
 }
 
-// Runs PCG on r (holding f) with x = 0 for nb right-hand sides. INIT_FF must have run.
-static jfft_status pcg_core(jfft_solver* h, int nb, int pc, double tol, int* status_out) {
+// Runs PCG in working precision T on w.r (holding the right-hand side) from x = 0
+// for nb right-hand sides. The INIT_FF stage must have run on w.r.
+template <typename T>
+static jfft_status pcg_core_t(jfft_solver* h, const Work<T>& w, int nb, int pc, double tol, int stop_mode,
+                              int* status_out) {
   const Grid& g = h->g;
   const int64_t fe = field_elems(h);
   int np = 0;
   jfft_status s;
-  CK(launch_fill(h->x, nb * fe, 0.0, h->st));
-  CK(launch_fill(h->p, nb * fe, 0.0, h->st));
-  s = precond(h, pc, h->r, h->z, nb, h->cg, &np);
-  if (s) return s;
-  CK(launch_cg_scalars(kStageInitGamma, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
-  CK(launch_cg_p(g, h->p, h->z, nb, fe, h->cg, h->st));
+  CK(cudaMemsetAsync(w.x, 0, nb * fe * sizeof(T), h->st));
+  CK(cudaMemsetAsync(w.p, 0, nb * fe * sizeof(T), h->st));
+  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np));
+  CK(launch_cg_scalars(kStageInitGamma, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
+  CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
   const int chunk = h->opt.check_every;
   int64_t launched = 0;
   const int64_t cap = (int64_t)h->max_iter + chunk;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      CK(launch_apply_K(g, h->ec, h->E, 0.0, h->p, h->q, nb, fe, nullptr, 1.0, 1, h->partial, &np, h->cg, h->st));
-      CK(launch_cg_scalars(kStageAlpha, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
-      CK(launch_cg_xr(g, h->x, h->r, h->p, h->q, nb, fe, h->cg, h->partial, &np, h->st));
-      CK(launch_cg_scalars(kStageRR, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
-      s = precond(h, pc, h->r, h->z, nb, h->cg, &np);
-      if (s) return s;
-      CK(launch_cg_scalars(kStageBeta, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
-      CK(launch_cg_p(g, h->p, h->z, nb, fe, h->cg, h->st));
+      CK(apply_op(h, w, w.p, w.q, nb, 1, &np, h->cg));
+      CK(launch_cg_scalars(kStageAlpha, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
+      CK(launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st));
+      CK(launch_cg_scalars(kStageRR, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
+      CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np));
+      CK(launch_cg_scalars(kStageBeta, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
+      CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
     }
     launched += chunk;
     CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
@@ -522,6 +605,81 @@ static jfft_status pcg_core(jfft_solver* h, int nb, int pc, double tol, int* sta
     else if (dn == kNoConv && worst != kBreakdown) worst = kNoConv;
   }
   *status_out = worst;
+  return JFFT_OK;
+}
+
+static jfft_status pcg_core(jfft_solver* h, int nb, int pc, double tol, int* status_out) {
+  return pcg_core_t<double>(h, work64(h), nb, pc, tol, h->opt.stop_mode, status_out);
+}
+
+// FP64 iterative refinement around the FP32 PCG (JFFT_PREC_MIXED). The right-hand
+// side is the macroscopic-strain load of h->shifts (macro) or the FP64 field f.
+// On return h->x holds u, its[b] the summed inner iterations, refine[b] the number
+// of inner solves, ff[b] = ||f||^2 and *status_out the worst outcome.
+static jfft_status solve_mixed(jfft_solver* h, int nb, int pc, double tol, bool macro, const double* f, int* its,
+                               int* refine, double* ff, int* status_out) {
+  const Grid& g = h->g;
+  const int64_t fe = field_elems(h);
+  const Work<float> w = work32(h);
+  int np = 0;
+  jfft_status s;
+  if (macro) {
+    CK(launch_apply_K(g, h->ec, h->E, 0.0, nullptr, h->r, nb, fe, h->shifts, -1.0, 2, h->partial, &np, nullptr,
+                      h->st));
+  } else {
+    CK(launch_dot<double>(g, f, f, nb, fe, h->partial, &np, h->st));
+  }
+  CK(launch_reduce_partials(h->partial, np, nb, kMaxPartials, h->red, h->st));
+  CK(cudaMemcpyAsync(h->red_h, h->red, nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemsetAsync(h->x, 0, nb * fe * sizeof(double), h->st));
+  s = sync(h);
+  if (s) return s;
+  for (int b = 0; b < nb; ++b) {
+    ff[b] = h->red_h[b];
+    its[b] = 0;
+    refine[b] = 0;
+  }
+  const int stop_mode = h->opt.stop_mode;
+  bool all_conv = false;
+  for (int k = 0; k <= h->opt.max_refine; ++k) {
+    // FP64 residual r = f - K u and its norm
+    if (macro) {
+      CK(launch_apply_K(g, h->ec, h->E, 0.0, h->x, h->r, nb, fe, h->shifts, -1.0, 2, h->partial, &np, nullptr,
+                        h->st));
+    } else {
+      CK(launch_apply_K(g, h->ec, h->E, 0.0, h->x, h->q, nb, fe, nullptr, 1.0, 0, nullptr, nullptr, nullptr, h->st));
+      CK(launch_sub_norm(g, f, h->q, h->r, nb, h->partial, &np, h->st));
+    }
+    CK(launch_reduce_partials(h->partial, np, nb, kMaxPartials, h->red, h->st));
+    CK(cudaMemcpyAsync(h->red_h, h->red, nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    s = sync(h);
+    if (s) return s;
+    bool any = false;
+    all_conv = true;
+    for (int b = 0; b < nb; ++b) {
+      const double rr = h->red_h[b];
+      const bool conv = ff[b] == 0.0 || (stop_mode == JFFT_STOP_REL ? rr <= tol * tol * ff[b] : rr <= tol);
+      all_conv = all_conv && conv;
+      h->active_h[b] = (!conv && k < h->opt.max_refine) ? 1 : 0;
+      any = any || h->active_h[b];
+    }
+    if (!any) break;
+    CK(cudaMemcpyAsync(h->active, h->active_h, nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(launch_to_f32(h->r, w.r, fe, nb, h->active, h->st));
+    CK(launch_dot<float>(g, w.r, w.r, nb, fe, h->partial, &np, h->st));
+    CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, nb, h->opt.inner_tol, JFFT_STOP_REL, h->max_iter,
+                         h->st));
+    int inner_status = kConverged;
+    s = pcg_core_t<float>(h, w, nb, pc, h->opt.inner_tol, JFFT_STOP_REL, &inner_status);
+    if (s) return s;
+    CK(launch_add_f32(h->x, w.x, nb * fe, h->st));
+    for (int b = 0; b < nb; ++b)
+      if (h->active_h[b]) {
+        its[b] += h->cg_h[b].iters;
+        refine[b] += 1;
+      }
+  }
+  *status_out = all_conv ? kConverged : kNoConv;
   return JFFT_OK;
 }
 
@@ -564,12 +722,19 @@ extern "C" jfft_status jfft_solve(jfft_solver* h, int n_loads, const double* eps
   const int64_t fe = field_elems(h);
   const int nb = n_loads;
   int np = 0;
-  // S2: r = f = -B^T W C eps_bar, ||f||^2
-  CK(launch_apply_K(g, h->ec, h->E, 0.0, nullptr, h->r, nb, fe, h->shifts, -1.0, 2, h->partial, &np, nullptr, h->st));
-  CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
   int st = kConverged;
-  s = pcg_core(h, nb, pc, tol, &st);
-  if (s) return s;
+  std::vector<int> mixed_its(nb, 0), mixed_ref(nb, 1);
+  std::vector<double> mixed_ff(nb, 0.0);
+  if (h->precision == JFFT_PREC_MIXED) {
+    s = solve_mixed(h, nb, pc, tol, true, nullptr, mixed_its.data(), mixed_ref.data(), mixed_ff.data(), &st);
+    if (s) return s;
+  } else {
+    // S2: r = f = -B^T W C eps_bar, ||f||^2
+    CK(launch_apply_K(g, h->ec, h->E, 0.0, nullptr, h->r, nb, fe, h->shifts, -1.0, 2, h->partial, &np, nullptr, h->st));
+    CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, nb, tol, h->opt.stop_mode, h->max_iter, h->st));
+    s = pcg_core(h, nb, pc, tol, &st);
+    if (s) return s;
+  }
   // S8: zero-mean fluctuation
   CK(launch_row_sums(h->x, nb * g.d, g.N, h->partial, &np, h->st));
   CK(launch_reduce_partials(h->partial, np, nb * g.d, kMaxPartials, h->red, h->st));
@@ -583,9 +748,15 @@ extern "C" jfft_status jfft_solve(jfft_solver* h, int n_loads, const double* eps
   CK(launch_stress(g, h->ec, h->E, h->x, nb, h->shifts, stress_dev, h->partial, &np, h->st));
   CK(launch_reduce_partials(h->partial, np, nb * h->ds, kMaxPartials, h->red + nb, h->st));
   CK(cudaMemcpyAsync(h->red_h, h->red, nb * (1 + h->ds) * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
+  if (h->precision != JFFT_PREC_MIXED)
+    CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
   s = sync(h);
   if (s) return s;
+  if (h->precision != JFFT_PREC_MIXED)
+    for (int b = 0; b < nb; ++b) {
+      mixed_ff[b] = h->cg_h[b].ff;
+      mixed_its[b] = h->cg_h[b].iters;
+    }
   if (res) {
     if (res->u) { s = copy_out(h, res->u, h->x, nb * fe * sizeof(double)); if (s) return s; }
     if (res->stress) {
@@ -601,21 +772,22 @@ extern "C" jfft_status jfft_solve(jfft_solver* h, int n_loads, const double* eps
       if (s) return s;
     }
     std::vector<double> chom(h->ds * nb), rel(nb);
-    std::vector<int> its(nb);
     for (int b = 0; b < nb; ++b) {
-      const double ff = h->cg_h[b].ff;
+      const double ff = mixed_ff[b];
       rel[b] = ff > 0.0 ? std::sqrt(h->red_h[b] / ff) : 0.0;
-      its[b] = h->cg_h[b].iters;
       for (int c = 0; c < h->ds; ++c) chom[c * nb + b] = h->red_h[nb + b * h->ds + c];
     }
     if (h->io == JFFT_MEM_DEVICE) {
       if (res->C_hom) CK(cudaMemcpy(res->C_hom, chom.data(), chom.size() * sizeof(double), cudaMemcpyHostToDevice));
       if (res->rel_res) CK(cudaMemcpy(res->rel_res, rel.data(), nb * sizeof(double), cudaMemcpyHostToDevice));
-      if (res->iters) CK(cudaMemcpy(res->iters, its.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+      if (res->iters) CK(cudaMemcpy(res->iters, mixed_its.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+      if (res->refine_steps)
+        CK(cudaMemcpy(res->refine_steps, mixed_ref.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
     } else {
       if (res->C_hom) std::memcpy(res->C_hom, chom.data(), chom.size() * sizeof(double));
       if (res->rel_res) std::memcpy(res->rel_res, rel.data(), nb * sizeof(double));
-      if (res->iters) std::memcpy(res->iters, its.data(), nb * sizeof(int));
+      if (res->iters) std::memcpy(res->iters, mixed_its.data(), nb * sizeof(int));
+      if (res->refine_steps) std::memcpy(res->refine_steps, mixed_ref.data(), nb * sizeof(int));
     }
   }
   s = sync(h);
@@ -661,7 +833,14 @@ extern "C" jfft_status jfft_apply_K(jfft_solver* h, int count, const double* x, 
   const int64_t fe = field_elems(h);
   s = copy_in(h, h->p, x, count * fe);
   if (s) return s;
-  CK(launch_apply_K(h->g, h->ec, h->E, 0.0, h->p, h->q, count, fe, nullptr, 1.0, 0, nullptr, nullptr, nullptr, h->st));
+  if (h->precision == JFFT_PREC_MIXED) {
+    CK(launch_to_f32(h->p, h->p32, count * fe, 1, nullptr, h->st));
+    CK(launch_apply_K_f32(h->g, h->ec, h->E32, h->p32, h->q32, count, fe, 0, nullptr, nullptr, nullptr, h->st));
+    CK(cudaMemsetAsync(h->q, 0, count * fe * sizeof(double), h->st));
+    CK(launch_add_f32(h->q, h->q32, count * fe, h->st));
+  } else {
+    CK(launch_apply_K(h->g, h->ec, h->E, 0.0, h->p, h->q, count, fe, nullptr, 1.0, 0, nullptr, nullptr, nullptr, h->st));
+  }
   s = copy_out(h, y, h->q, count * fe * sizeof(double));
   if (s) return s;
   return sync(h);
@@ -712,8 +891,15 @@ extern "C" jfft_status jfft_apply_precond(jfft_solver* h, int pc, int count, con
   s = copy_in(h, h->r, r, count * fe);
   if (s) return s;
   int np = 0;
-  s = precond(h, pc, h->r, h->z, count, nullptr, &np);
-  if (s) return s;
+  if (h->precision == JFFT_PREC_MIXED) {
+    CK(launch_to_f32(h->r, h->r32, count * fe, 1, nullptr, h->st));
+    CK(precond_op(h, work32(h), pc, h->r32, h->z32, count, nullptr, &np));
+    CK(cudaMemsetAsync(h->z, 0, count * fe * sizeof(double), h->st));
+    CK(launch_add_f32(h->z, h->z32, count * fe, h->st));
+  } else {
+    s = precond(h, pc, h->r, h->z, count, nullptr, &np);
+    if (s) return s;
+  }
   s = copy_out(h, z, h->z, count * fe * sizeof(double));
   if (s) return s;
   return sync(h);
@@ -729,18 +915,26 @@ extern "C" jfft_status jfft_solve_rhs(jfft_solver* h, int count, const double* f
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, JFFT_ERR_ARG, "tol must be finite and >= 0");
   if (!valid_pc(pc)) return fail(h, JFFT_ERR_ARG, "unknown preconditioner");
   const int64_t fe = field_elems(h);
-  s = copy_in(h, h->r, f, count * fe);
-  if (s) return s;
   int np = 0;
-  CK(launch_dot(h->g, h->r, h->r, count, fe, h->partial, &np, h->st));
-  CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, count, tol, h->opt.stop_mode, h->max_iter, h->st));
   int st = kConverged;
-  s = pcg_core(h, count, pc, tol, &st);
-  if (s) return s;
+  std::vector<int> its(count, 0), ref(count, 1);
+  if (h->precision == JFFT_PREC_MIXED) {
+    s = copy_in(h, h->z, f, count * fe);  // the FP64 z buffer is free in mixed mode
+    if (s) return s;
+    std::vector<double> ff(count);
+    s = solve_mixed(h, count, pc, tol, false, h->z, its.data(), ref.data(), ff.data(), &st);
+    if (s) return s;
+  } else {
+    s = copy_in(h, h->r, f, count * fe);
+    if (s) return s;
+    CK(launch_dot<double>(h->g, h->r, h->r, count, fe, h->partial, &np, h->st));
+    CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, count, tol, h->opt.stop_mode, h->max_iter, h->st));
+    s = pcg_core(h, count, pc, tol, &st);
+    if (s) return s;
+    for (int b = 0; b < count; ++b) its[b] = h->cg_h[b].iters;
+  }
   if (u) { s = copy_out(h, u, h->x, count * fe * sizeof(double)); if (s) return s; }
   if (iters) {
-    std::vector<int> its(count);
-    for (int b = 0; b < count; ++b) its[b] = h->cg_h[b].iters;
     if (h->io == JFFT_MEM_DEVICE) CK(cudaMemcpy(iters, its.data(), count * sizeof(int), cudaMemcpyHostToDevice));
     else std::memcpy(iters, its.data(), count * sizeof(int));
   }

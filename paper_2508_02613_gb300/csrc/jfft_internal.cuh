@@ -44,13 +44,30 @@ struct Grid {
 //   nrm[k][a][b] = (a == b ? lambda + 2 mu : lambda) kappa_k gs_a gs_b,
 //   shr[k][a][b] = mu kappa_k gs_a gs_b.
 // Nodal forces are the inverse transform of F times E_e.
-struct ElemConst {
-  double nrm[3][3][3];
-  double shr[3][3][3];
-  double gs[3];       // (2 / h_a) / 2^d: mode -> displacement-gradient factor
-  double lam, mu;     // Lame constants of the unit material
-  double vol;         // element volume
+template <typename T> struct ElemConstT {
+  T nrm[3][3][3];
+  T shr[3][3][3];
+  T gs[3];       // (2 / h_a) / 2^d: mode -> displacement-gradient factor
+  T lam, mu;     // Lame constants of the unit material
+  T vol;         // element volume
 };
+using ElemConst = ElemConstT<double>;
+
+// The same constants rounded to another working precision.
+template <typename T> inline ElemConstT<T> elem_const_as(const ElemConst& e) {
+  ElemConstT<T> o;
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        o.nrm[k][a][b] = (T)e.nrm[k][a][b];
+        o.shr[k][a][b] = (T)e.shr[k][a][b];
+      }
+  for (int a = 0; a < 3; ++a) o.gs[a] = (T)e.gs[a];
+  o.lam = (T)e.lam;
+  o.mu = (T)e.mu;
+  o.vol = (T)e.vol;
+  return o;
+}
 
 // Macroscopic strain of one load case expressed as a shift of the single-axis
 // modes: W_a[{b}] += shift[a][b] turns B u into eps_bar + B u at every Gauss point.
@@ -106,6 +123,11 @@ cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, 
 cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const double* E, const double* x, double* y,
                                       double* partial, int cap, int* nparts, cudaStream_t st);
 
+// FP32 operator for the mixed-precision inner solve (no strain shift).
+cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* E, const float* x, float* y, int nb,
+                               int64_t field_stride, int dot_mode, double* partial, int* nparts, const CgState* cg,
+                               cudaStream_t st);
+
 // S8: element-averaged Mandel stress [nb][d*][N] (stress may be NULL) and partial
 // sums of vol * stress in partial[(b d* + s) * kMaxPartials + blk].
 cudaError_t launch_stress(const Grid& g, const ElemConst& ec, const double* E, const double* u, int nb,
@@ -127,18 +149,23 @@ cudaError_t launch_green_export(const Grid& g, const double* G, double* out, dou
 // S6: twiddle table exp(-2 pi i m / n), m < n.
 cudaError_t launch_twiddles(double2* tw, int n, cudaStream_t st);
 
-struct FftPlan {
-  const double2* tw[3];
-  double2* T;        // spectrum buffer (real-axis pass output)
-  double2* U;        // second spectrum buffer (3D)
-  const double* G;   // stored symbol table [F][d*]
+template <typename R> struct FftPlanT {
+  const cplx<R>* tw[3];
+  cplx<R>* T;        // spectrum buffer (real-axis pass output)
+  cplx<R>* U;        // second spectrum buffer (3D)
+  const R* G;        // stored symbol table [F][d*]
 };
+using FftPlan = FftPlanT<double>;
 
 // S5 + S6: z_b = M^-1 r_b (Green, or Green-Jacobi when jacobi), with the partial
 // sums of r.z. jscale[a] = kappa_a^-1/2; void nodes use void_js.
 cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
                                  int64_t field_stride, const double* js, const double* jscale, double void_js,
                                  bool jacobi, double* partial, int* nparts, const CgState* cg, cudaStream_t st);
+// The same in FP32 (mixed-precision inner solve).
+cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
+                                     const float* js, const double* jscale, double void_js, bool jacobi,
+                                     double* partial, int* nparts, const CgState* cg, cudaStream_t st);
 // Forward transform of nb d-component real fields -> line-major spectrum [nb][d][F].
 cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
                                     const double2** spec_out, cudaStream_t st);
@@ -147,12 +174,25 @@ cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int
                                   const double* jscale, double void_js, bool identity, double* partial, int* nparts,
                                   const CgState* cg, cudaStream_t st);
 
-// S4: CG vector updates and inner products.
-cudaError_t launch_cg_xr(const Grid& g, double* x, double* r, const double* p, const double* q, int nb, int64_t stride,
-                         CgState* cg, double* partial, int* nparts, cudaStream_t st);
-cudaError_t launch_cg_p(const Grid& g, double* p, const double* z, int nb, int64_t stride, CgState* cg, cudaStream_t st);
-cudaError_t launch_dot(const Grid& g, const double* a, const double* c, int nb, int64_t stride, double* partial,
-                       int* nparts, cudaStream_t st);
+// S4: CG vector updates and inner products (T = double or float; scalars in FP64).
+template <typename T>
+cudaError_t launch_cg_xr(const Grid& g, T* x, T* r, const T* p, const T* q, int nb, int64_t stride, CgState* cg,
+                         double* partial, int* nparts, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cg_p(const Grid& g, T* p, const T* z, int nb, int64_t stride, CgState* cg, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dot(const Grid& g, const T* a, const T* c, int nb, int64_t stride, double* partial, int* nparts,
+                       cudaStream_t st);
+// FP32 variant of the Jacobi / identity preconditioner.
+cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
+                                      const double* jscale, double void_js, bool identity, double* partial,
+                                      int* nparts, const CgState* cg, cudaStream_t st);
+// Precision conversions for the refinement loop: dst = (float) src per rhs, zeroed
+// where active[b] == 0; u += (double) d; r = f - q with partial sums of r.r.
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n_per_rhs, int nb, const int* active, cudaStream_t st);
+cudaError_t launch_add_f32(double* u, const float* d, int64_t n, cudaStream_t st);
+cudaError_t launch_sub_norm(const Grid& g, const double* f, const double* q, double* r, int nb, double* partial,
+                            int* nparts, cudaStream_t st);
 // S4 / S7: scalar stages, one block per rhs.
 enum ScalarStage { kStageInitFF = 0, kStageInitGamma = 1, kStageAlpha = 2, kStageRR = 3, kStageBeta = 4 };
 cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,

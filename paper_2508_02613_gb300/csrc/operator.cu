@@ -57,26 +57,29 @@ struct MarchGeom {
 template <int D> __host__ __device__ inline int plane_nodes(const MarchGeom& m) { return (m.P1 + 2) * (D == 3 ? m.P2 + 2 : 1); }
 template <int D> __host__ __device__ inline int plane_elems(const MarchGeom& m) { return (m.P1 + 1) * (D == 3 ? m.P2 + 1 : 1); }
 
-template <int D> static size_t march_smem(const MarchGeom& m) {
+template <int D, typename T = double> static size_t march_smem(const MarchGeom& m) {
   const int pn = plane_nodes<D>(m), pe = plane_elems<D>(m);
-  return sizeof(double) * (size_t(2) * D * pn + pe + size_t(D) * (1 << D) * pe);
+  return sizeof(T) * (size_t(2) * D * pn + pe + size_t(D) * (1 << D) * pe);
 }
 
+// T: working precision of fields, material and constants (double or float); the
+// dot partial is accumulated per thread in T and across the block in double.
 // DOT: 0 none, 1 sum x.y, 2 sum y.y
-template <int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
-__global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst ec, const double* __restrict__ E,
-                                                 double e_uniform, const double* __restrict__ x, double* __restrict__ y,
-                                                 int64_t fstride, const StrainShift* __restrict__ shifts, double sgn,
+template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
+__global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConstT<T> ec, const T* __restrict__ E,
+                                                 T e_uniform, const T* __restrict__ x, T* __restrict__ y,
+                                                 int64_t fstride, const StrainShift* __restrict__ shifts, T sgn,
                                                  double* __restrict__ partial, const CgState* __restrict__ cg) {
   constexpr int NC = 1 << D;
   constexpr int NCP = NC / 2;  // in-plane corners
   const int b = blockIdx.z;
   if (cg && cg[b].done) return;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   const int pn = plane_nodes<D>(mg), pe = plane_elems<D>(mg);
-  double* ring = sm;                       // [2][D][pn]
-  double* Es = ring + 2 * D * pn;          // [pe]
-  double* Fs = Es + pe;                    // [D][2][NCP][pe]
+  T* ring = sm;                            // [2][D][pn]
+  T* Es = ring + 2 * D * pn;               // [pe]
+  T* Fs = Es + pe;                         // [D][2][NCP][pe]
 
   const int n0 = g.n[0], n1 = g.n[1], n2 = (D == 3 ? g.n[2] : 1);
   const int64_t plane = (int64_t)n1 * n2;
@@ -85,8 +88,8 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
   const int L0 = blockIdx.y * mg.seg;
   const int W1 = mg.P1 + 2, W2 = (D == 3 ? mg.P2 + 2 : 1);   // halo tile dims (nodes)
   const int E1 = mg.P1 + 1, E2 = (D == 3 ? mg.P2 + 1 : 1);   // element tile dims
-  const double* xb = HAS_X ? x + (int64_t)b * fstride : nullptr;
-  double* yb = y + (int64_t)b * fstride;
+  const T* xb = HAS_X ? x + (int64_t)b * fstride : nullptr;
+  T* yb = y + (int64_t)b * fstride;
   StrainShift sh;
   if (SHIFT) sh = shifts[b];
 
@@ -103,14 +106,14 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
       const int gi2 = (D == 3 ? (i2s - 1 + h2 + n2) % n2 : 0);
       const int64_t node = (int64_t)l * plane + (int64_t)gi1 * n2 + gi2;
 #pragma unroll
-      for (int a = 0; a < D; ++a) ring[(slot * D + a) * pn + idx] = HAS_X ? xb[a * g.N + node] : 0.0;
+      for (int a = 0; a < D; ++a) ring[(slot * D + a) * pn + idx] = HAS_X ? xb[a * g.N + node] : T(0);
     }
   };
 
-  double carry[D];
+  T carry[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) carry[a] = 0.0;
-  double dot = 0.0;
+  for (int a = 0; a < D; ++a) carry[a] = T(0);
+  T dot = T(0);
 
   if (HAS_X) load_layer(L0 - 1, (L0 - 1) & 1);
   for (int e0 = L0 - 1; e0 < L0 + mg.seg; ++e0) {
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
     const int s0 = e0 & 1, s1 = (e0 + 1) & 1;
     for (int idx = tid; idx < pe; idx += blockDim.x) {
       const int h1 = idx / E2, h2 = idx % E2;
-      double u[D][NC];
+      T u[D][NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int o0 = (c >> (D - 1)) & 1;
@@ -136,10 +139,10 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
         const int o2 = (D == 3 ? c & 1 : 0);
         const int node = (h1 + o1) * W2 + (h2 + o2);
 #pragma unroll
-        for (int a = 0; a < D; ++a) u[a][c] = HAS_X ? ring[((o0 ? s1 : s0) * D + a) * pn + node] : 0.0;
+        for (int a = 0; a < D; ++a) u[a][c] = HAS_X ? ring[((o0 ? s1 : s0) * D + a) * pn + node] : T(0);
       }
-      const double Ee = HAS_E ? Es[idx] : e_uniform;
-      element_force<D, double, SHIFT>(ec, &sh, u, Ee);
+      const T Ee = HAS_E ? Es[idx] : e_uniform;
+      element_force<D, T, SHIFT>(ec, &sh, u, Ee);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int o0 = (c >> (D - 1)) & 1;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
     if (owner) {
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        double add0 = 0.0, add1 = 0.0;
+        T add0 = T(0), add1 = T(0);
 #pragma unroll
         for (int cin = 0; cin < NCP; ++cin) {
           const int o1 = (D == 3 ? (cin >> 1) & 1 : cin & 1);
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
           add1 += Fs[((a * 2 + 1) * NCP + cin) * pe + el];
         }
         if (e0 >= L0) {
-          const double q = sgn * (carry[a] + add0);
+          const T q = sgn * (carry[a] + add0);
           const int l = e0;  // < n0 by construction
           const int64_t node = (int64_t)l * plane + (int64_t)(i1s + own1) * n2 + (D == 3 ? i2s + own2 : 0);
           yb[a * g.N + node] = q;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
     __syncthreads();
   }
   if (DOT) {
-    const double s = block_sum(dot);
+    const double s = block_sum((double)dot);
     if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
   }
 }
@@ -198,19 +201,19 @@ template <int D> static MarchGeom march_geom(const Grid& g) {
   return m;
 }
 
-template <int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
-static cudaError_t apply_K_t(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
-                             double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, double* partial,
+template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
+static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x,
+                             T* y, int nb, int64_t fstride, const StrainShift* shifts, T sgn, double* partial,
                              int* nparts, const CgState* cg, cudaStream_t st) {
   MarchGeom m = march_geom<D>(g);
-  const size_t smem = march_smem<D>(m);
-  auto kern = k_apply_K<D, DOT, HAS_X, HAS_E, SHIFT>;
+  const size_t smem = march_smem<D, T>(m);
+  auto kern = k_apply_K<T, D, DOT, HAS_X, HAS_E, SHIFT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, nb);
   // one element per thread per layer; warps round up (owners are the first P1*P2)
   const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;
-  const char* kname = DOT == 1 ? "apply_K"
+  const char* kname = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain") : DOT == 1 ? "apply_K"
                       : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
   JFFT_K(kname, st, kern<<<grid, threads, smem, st>>>(g, m, ec, E, e_uniform, x, y, fstride, shifts, sgn, partial, cg));
   if (nparts) *nparts = grid.x * grid.y;
@@ -224,7 +227,7 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
   const bool hx = x != nullptr, he = E != nullptr, sh = shifts != nullptr;
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
-    return apply_K_t<D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st);
+    return apply_K_t<double, D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st);
   JFFT_AK(1, true, true, false)   // CG: q = K p, p.q
   JFFT_AK(0, true, true, false)   // plain apply
   JFFT_AK(0, true, false, false)  // reference operator (uniform E)
@@ -256,7 +259,7 @@ static cudaError_t apply_K_dot_capped_t(const Grid& g, const ElemConst& ec, cons
   while (tiles * (g.n[0] / m.seg) > cap && m.seg < g.n[0]) m.seg *= 2;
   if (tiles * (g.n[0] / m.seg) > cap) return cudaErrorInvalidValue;
   const size_t smem = march_smem<D>(m);
-  auto kern = k_apply_K<D, 1, true, true, false>;
+  auto kern = k_apply_K<double, D, 1, true, true, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, 1);
@@ -271,6 +274,27 @@ cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const 
                                       double* partial, int cap, int* nparts, cudaStream_t st) {
   if (g.d == 2) return apply_K_dot_capped_t<2>(g, ec, E, x, y, partial, cap, nparts, st);
   return apply_K_dot_capped_t<3>(g, ec, E, x, y, partial, cap, nparts, st);
+}
+
+// Working-precision FP32 operator (mixed-precision inner solve): y = K x with the
+// material in FP32, optional fused x.y partials (dot_mode 1) or none (0).
+template <int D>
+static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, const float* E, const float* x, float* y,
+                                 int nb, int64_t fstride, int dot_mode, double* partial, int* nparts, const CgState* cg,
+                                 cudaStream_t st) {
+  if (dot_mode == 1)
+    return apply_K_t<float, D, 1, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
+                                                    st);
+  return apply_K_t<float, D, 0, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
+                                                  st);
+}
+
+cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* E, const float* x, float* y, int nb,
+                               int64_t field_stride, int dot_mode, double* partial, int* nparts, const CgState* cg,
+                               cudaStream_t st) {
+  const ElemConstT<float> ecf = elem_const_as<float>(ec);
+  if (g.d == 2) return apply_K_f32_d<2>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st);
+  return apply_K_f32_d<3>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st);
 }
 
 // ------------------------------------------------------------------ S8

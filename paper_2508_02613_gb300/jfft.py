@@ -23,6 +23,7 @@ PRECOND = {"none": -1, "green": 0, "green_jacobi": 1, "jacobi": 2}
 MATERIAL = {"young": 0, "density": 1}
 STOP = {"rel": 0, "abs_sq": 1}
 MEM = {"host": 0, "device": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
 DIAG = {"closed_form": 0, "combs": 1}
 
 
@@ -38,12 +39,12 @@ class JfftMaterial(ctypes.Structure):
 class JfftOptions(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("stop_mode", c_int), ("stream", c_void_p),
                 ("hbm_budget", c_size_t), ("check_every", c_int), ("io_memory", c_int), ("max_loads", c_int),
-                ("void_value", c_double), ("device", c_int)]
+                ("void_value", c_double), ("device", c_int), ("inner_tol", c_double), ("max_refine", c_int)]
 
 
 class JfftResult(ctypes.Structure):
     _fields_ = [("u", c_void_p), ("stress", c_void_p), ("C_hom", c_void_p), ("iters", c_void_p),
-                ("rel_res", c_void_p)]
+                ("rel_res", c_void_p), ("refine_steps", c_void_p)]
 
 
 class JfftError(RuntimeError):
@@ -144,7 +145,8 @@ class Solver:
 
     def __init__(self, shape, field, nu, kind="young", e_min=0.0, e_max=1.0, exponent=1.0, C_ref=None,
                  max_iter=100000, stop_mode="rel", stream=None, check_every=8, io="host", max_loads=6,
-                 void_value=1.0, device=0, hbm_budget=0, pinned=False):
+                 void_value=1.0, device=0, hbm_budget=0, pinned=False, precision="fp64", inner_tol=1e-3,
+                 max_refine=30):
         self.lib = load()
         self.pinned = pinned
         self.shape = tuple(int(s) for s in shape)
@@ -167,6 +169,10 @@ class Solver:
         opt.void_value = void_value
         opt.device = device
         opt.hbm_budget = hbm_budget
+        opt.precision = PRECISION[precision]
+        opt.inner_tol = inner_tol
+        opt.max_refine = max_refine
+        self.precision = precision
         self.max_loads = max(max_loads, self.d)
         h = c_void_p()
         cref = None if C_ref is None else _f64(C_ref).reshape(-1)
@@ -242,10 +248,12 @@ class Solver:
         chom = self._out((self.ds, nl))
         its = self._out((nl,), np.int32)
         rel = self._out((nl,))
-        res = JfftResult(_ptr(u), _ptr(stress), _ptr(chom), _ptr(its), _ptr(rel))
+        ref = self._out((nl,), np.int32)
+        res = JfftResult(_ptr(u), _ptr(stress), _ptr(chom), _ptr(its), _ptr(rel), _ptr(ref))
         st = self._check(self.lib.jfft_solve(self.h, nl, _ptr(eps), float(tol), PRECOND[precond], ctypes.byref(res)),
                          allow=(JFFT_ERR_NOCONV, JFFT_ERR_BREAKDOWN))
-        return {"u": u, "stress": stress, "C_hom": chom, "iters": its, "rel_res": rel, "status": st}
+        return {"u": u, "stress": stress, "C_hom": chom, "iters": its, "rel_res": rel, "refine_steps": ref,
+                "status": st}
 
     def get_material(self):
         E = self._out(self.shape)

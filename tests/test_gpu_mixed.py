@@ -1,0 +1,89 @@
+"""Mixed precision (FP32 inner PCG inside FP64 iterative refinement) against the
+FP64 oracle, through the C ABI.
+
+Tolerances: single FP32 applications are compared at 2e-6 (operator: sums of ~10
+FP32 terms; preconditioner: FP32 transforms of log2 N stages) relative to the
+oracle's max; solves are judged on the true FP64 relative residual, which the
+refinement drives to the requested tolerance, and on the solution's distance to
+the oracle's, bounded like two FP64 runs at that tolerance (10 tau)."""
+
+import numpy as np
+import pytest
+
+from oracle import assemble, fe, material, solve as osolve
+from synthetic import mandel_unit_loads, random_field, smooth_density
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _solver(shape, rho, contrast=1e4, **kw):
+    from paper_2508_02613_gb300.jfft import Solver
+    return Solver(shape, rho, 0.3, kind="density", e_min=1.0 / contrast, e_max=1.0, exponent=2.0,
+                  precision="mixed", **kw)
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
+
+
+@pytest.mark.parametrize("shape", [(8, 16), (64, 512), (8, 4, 16), (16, 16, 64)])
+def test_fp32_operator_and_preconditioners(shape):
+    d = len(shape)
+    rho = smooth_density(shape, 8, 3.0, 1)
+    E = material.young_from_density(rho, 1e-4, 1.0, 2.0)
+    s = _solver(shape, rho)
+    prob = osolve.setup(shape, E, 0.3)
+    x = random_field((2, d) + shape, 3)
+    want = np.stack([assemble.apply(prob.K, x[i]) for i in range(2)])
+    assert rel(s.apply_K(x), want) <= 2e-6
+    for pc in ("green", "green_jacobi", "jacobi"):
+        z = s.apply_precond(pc, x)
+        zw = np.stack([prob.minv(pc)(x[i]) for i in range(2)])
+        assert rel(z, zw) <= 2e-6, pc
+
+
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+@pytest.mark.parametrize("tol", [1e-8, 1e-11])
+def test_mixed_solve_reaches_fp64_residual(pc, tol):
+    shape = (32, 32)
+    rho = smooth_density(shape, 16, 4.0, 0)
+    E = material.young_from_density(rho, 1e-4, 1.0, 2.0)
+    s = _solver(shape, rho)
+    eps = mandel_unit_loads(2)
+    out = s.solve(eps, tol, pc)
+    assert out["status"] == 0
+    assert np.all(out["rel_res"] <= tol * 1.01)
+    assert np.all(out["refine_steps"] >= 2)
+    prob = osolve.setup(shape, E, 0.3)
+    ref = osolve.solve(prob, eps, 1e-13, pc)
+    du = max(np.linalg.norm(out["u"][g] - ref.u[g]) / np.linalg.norm(ref.u[g]) for g in range(3))
+    dc = rel(out["C_hom"], ref.C_hom)
+    print(f"mixed {pc} tol {tol:g}: rel_res {out['rel_res']}, u diff {du:.2e}, C_hom diff {dc:.2e}, "
+          f"iters {out['iters']}, refine {out['refine_steps']}")
+    assert du <= 1e4 * tol, du
+    assert dc <= 10 * tol, dc
+
+
+def test_mixed_solve_3d_and_rhs():
+    shape = (8, 8, 16)
+    rho = smooth_density(shape, 8, 3.0, 4)
+    E = material.young_from_density(rho, 1e-3, 1.0, 3.0)
+    from paper_2508_02613_gb300.jfft import Solver
+    s = Solver(shape, rho, 0.3, kind="density", e_min=1e-3, e_max=1.0, exponent=3.0, precision="mixed")
+    eps = mandel_unit_loads(3)
+    out = s.solve(eps, 1e-9, "green_jacobi")
+    assert out["status"] == 0 and np.all(out["rel_res"] <= 1e-9 * 1.01)
+    prob = osolve.setup(shape, E, 0.3)
+    ref = osolve.solve(prob, eps, 1e-13, "green_jacobi")
+    assert rel(out["C_hom"], ref.C_hom) <= 1e-8
+    f = assemble.assemble_rhs(shape, E, prob.C, eps[5])
+    r = s.solve_rhs(f[None], 1e-9, "green")
+    assert r["status"] == 0
+    u = r["u"][0] - r["u"][0].mean(axis=(1, 2, 3), keepdims=True)
+    assert np.linalg.norm(f - assemble.apply(prob.K, u)) <= 1.01e-9 * np.linalg.norm(f)
