@@ -16,41 +16,67 @@ static int vec_blocks(int64_t n2) {  // n2 = number of 2-vectors per rhs
 
 template <typename T> static const char* nm(const char* d64, const char* d32) { return sizeof(T) == 8 ? d64 : d32; }
 
-// x += alpha p ; r -= alpha q ; partial ||r||^2
+// 16-byte vectors of the working precision (four floats or two doubles).
+template <typename T> struct V16;
+template <> struct V16<float> { using t = float4; static constexpr int n = 4; };
+template <> struct V16<double> { using t = double2; static constexpr int n = 2; };
+
+static int vec16_blocks(int64_t n16) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n16 + 511) / 512, 152 * 4));
+}
+
+// x += alpha p ; r -= alpha q ; partial ||r||^2. Each thread handles two 16-byte
+// vectors per loop trip so that more loads are in flight.
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_xr(cplx<T>* __restrict__ x, cplx<T>* __restrict__ r,
-                                               const cplx<T>* __restrict__ p, const cplx<T>* __restrict__ q,
-                                               int64_t n2, int64_t stride2, const CgState* __restrict__ cg,
-                                               double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_cg_xr(typename V16<T>::t* __restrict__ x, typename V16<T>::t* __restrict__ r,
+                                               const typename V16<T>::t* __restrict__ p,
+                                               const typename V16<T>::t* __restrict__ q, int64_t n16, int64_t stride16,
+                                               const CgState* __restrict__ cg, double* __restrict__ partial) {
+  using V = typename V16<T>::t;
+  constexpr int NV = V16<T>::n;
   const int b = blockIdx.y;
   if (cg[b].done) return;
   const T al = (T)cg[b].alpha;
-  const int64_t off = (int64_t)b * stride2;
+  const int64_t off = (int64_t)b * stride16;
   T acc = T(0);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-    cplx<T> xv = x[off + i], rv = r[off + i];
-    const cplx<T> pv = p[off + i], qv = q[off + i];
-    xv.x = fma(al, pv.x, xv.x);
-    xv.y = fma(al, pv.y, xv.y);
-    rv.x = fma(-al, qv.x, rv.x);
-    rv.y = fma(-al, qv.y, rv.y);
-    x[off + i] = xv;
-    r[off + i] = rv;
-    acc = fma(rv.x, rv.x, acc);
-    acc = fma(rv.y, rv.y, acc);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += 2 * step) {
+    const int64_t i2 = i + step;
+    const bool two = i2 < n16;
+    V xv[2], rv[2], pv[2], qv[2];
+    xv[0] = x[off + i]; rv[0] = r[off + i]; pv[0] = p[off + i]; qv[0] = q[off + i];
+    if (two) { xv[1] = x[off + i2]; rv[1] = r[off + i2]; pv[1] = p[off + i2]; qv[1] = q[off + i2]; }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      T* xa = reinterpret_cast<T*>(&xv[u]);
+      T* ra = reinterpret_cast<T*>(&rv[u]);
+      const T* pa = reinterpret_cast<const T*>(&pv[u]);
+      const T* qa = reinterpret_cast<const T*>(&qv[u]);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        xa[c] = fma(al, pa[c], xa[c]);
+        ra[c] = fma(-al, qa[c], ra[c]);
+        acc = fma(ra[c], ra[c], acc);
+      }
+    }
+    x[off + i] = xv[0];
+    r[off + i] = rv[0];
+    if (two) { x[off + i2] = xv[1]; r[off + i2] = rv[1]; }
   }
-  const double s = block_sum((double)acc);
-  if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
+  const double sm = block_sum((double)acc);
+  if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = sm;
 }
 
 template <typename T>
 cudaError_t launch_cg_xr(const Grid& g, T* x, T* r, const T* p, const T* q, int nb, int64_t stride, CgState* cg,
                          double* partial, int* nparts, cudaStream_t st) {
-  const int64_t n2 = g.d * g.N / 2;
-  const int bl = vec_blocks(n2);
+  using V = typename V16<T>::t;
+  const int64_t n16 = g.d * g.N / V16<T>::n;
+  const int bl = vec16_blocks(n16);
   JFFT_K(nm<T>("cg_xr", "cg_xr_f32"), st,
-         k_cg_xr<T><<<dim3(bl, nb), 256, 0, st>>>((cplx<T>*)x, (cplx<T>*)r, (const cplx<T>*)p, (const cplx<T>*)q, n2,
-                                                  stride / 2, cg, partial));
+         k_cg_xr<T><<<dim3(bl, nb), 256, 0, st>>>((V*)x, (V*)r, (const V*)p, (const V*)q, n16, stride / V16<T>::n,
+                                                  cg, partial));
   *nparts = bl;
   return cudaGetLastError();
 }
@@ -61,26 +87,39 @@ template cudaError_t launch_cg_xr<float>(const Grid&, float*, float*, const floa
 
 // p = z + beta p
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_p(cplx<T>* __restrict__ p, const cplx<T>* __restrict__ z, int64_t n2,
-                                              int64_t stride2, const CgState* __restrict__ cg) {
+__global__ void __launch_bounds__(256) k_cg_p(typename V16<T>::t* __restrict__ p, const typename V16<T>::t* __restrict__ z,
+                                              int64_t n16, int64_t stride16, const CgState* __restrict__ cg) {
+  using V = typename V16<T>::t;
+  constexpr int NV = V16<T>::n;
   const int b = blockIdx.y;
   if (cg[b].done) return;
   const T be = (T)cg[b].beta;
-  const int64_t off = (int64_t)b * stride2;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-    cplx<T> pv = p[off + i];
-    const cplx<T> zv = z[off + i];
-    pv.x = fma(be, pv.x, zv.x);
-    pv.y = fma(be, pv.y, zv.y);
-    p[off + i] = pv;
+  const int64_t off = (int64_t)b * stride16;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += 2 * step) {
+    const int64_t i2 = i + step;
+    const bool two = i2 < n16;
+    V pv[2], zv[2];
+    pv[0] = p[off + i]; zv[0] = z[off + i];
+    if (two) { pv[1] = p[off + i2]; zv[1] = z[off + i2]; }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      T* pa = reinterpret_cast<T*>(&pv[u]);
+      const T* za = reinterpret_cast<const T*>(&zv[u]);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) pa[c] = fma(be, pa[c], za[c]);
+    }
+    p[off + i] = pv[0];
+    if (two) p[off + i2] = pv[1];
   }
 }
 
 template <typename T>
 cudaError_t launch_cg_p(const Grid& g, T* p, const T* z, int nb, int64_t stride, CgState* cg, cudaStream_t st) {
-  const int64_t n2 = g.d * g.N / 2;
+  using V = typename V16<T>::t;
+  const int64_t n16 = g.d * g.N / V16<T>::n;
   JFFT_K(nm<T>("cg_p", "cg_p_f32"), st,
-         k_cg_p<T><<<dim3(vec_blocks(n2), nb), 256, 0, st>>>((cplx<T>*)p, (const cplx<T>*)z, n2, stride / 2, cg));
+         k_cg_p<T><<<dim3(vec16_blocks(n16), nb), 256, 0, st>>>((V*)p, (const V*)z, n16, stride / V16<T>::n, cg));
   return cudaGetLastError();
 }
 template cudaError_t launch_cg_p<double>(const Grid&, double*, const double*, int, int64_t, CgState*, cudaStream_t);

@@ -1,0 +1,175 @@
+// Register-resident Stockham engine for one line of length L (power of two).
+//
+// A line is handled by TPL = L / RM_eff threads (RM_eff = min(RM, L)); lane j of a
+// line holds RM_eff values. The first stage takes its inputs from registers
+// (positions j + TPL r) and runs radix RM_eff; later stages read their inputs from
+// shared memory at Stockham positions b + r L/R, multiply by table twiddles
+// W_{Ns R}^{r k}, run an in-register DFT of size R (16, 8, 4 or 2) and write
+// (b - k) R + k + r Ns, alternating between two buffers with one barrier per stage.
+// The result is left in natural order in the returned buffer.
+//
+// Shared-memory layout of a line: element p lives at spad(p) = p + p / 16. The
+// stride-R writes of the first stages would otherwise put all lanes of a warp on
+// the same banks; with the padding every stage's reads and writes are
+// conflict-free for 8-byte elements.
+#pragma once
+
+#include "jfft_internal.cuh"
+
+namespace jfft {
+
+__host__ __device__ __forceinline__ int spad(int p) { return p + (p >> 4); }
+// Shared-memory slots of a line holding elements 0..n (inclusive).
+__host__ __device__ __forceinline__ int line_slots(int n) { return spad(n) + 1; }
+
+template <typename T> __device__ __forceinline__ cplx<T> c_add(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cplx<T> c_sub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cplx<T> c_mul(cplx<T> a, cplx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV> __device__ __forceinline__ cplx<T> c_mi(cplx<T> a) {
+  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+// In-register DFT of size R, natural order in and out.
+template <typename T, int R, bool INV> struct Dft;
+
+template <typename T, bool INV> struct Dft<T, 1, INV> {
+  __device__ __forceinline__ static void run(cplx<T>*) {}
+};
+
+template <typename T, bool INV> struct Dft<T, 2, INV> {
+  __device__ __forceinline__ static void run(cplx<T>* v) {
+    const cplx<T> a = v[0], b = v[1];
+    v[0] = c_add<T>(a, b);
+    v[1] = c_sub<T>(a, b);
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 4, INV> {
+  __device__ __forceinline__ static void run(cplx<T>* v) {
+    const cplx<T> s02 = c_add<T>(v[0], v[2]), d02 = c_sub<T>(v[0], v[2]);
+    const cplx<T> s13 = c_add<T>(v[1], v[3]), d13 = c_mi<T, INV>(c_sub<T>(v[1], v[3]));
+    v[0] = c_add<T>(s02, s13);
+    v[2] = c_sub<T>(s02, s13);
+    v[1] = c_add<T>(d02, d13);
+    v[3] = c_sub<T>(d02, d13);
+  }
+};
+
+// Radix-2 split of a size-2H DFT into two size-H DFTs (even / odd samples):
+// X[k] = E[k] + W^k O[k], X[k + H] = E[k] - W^k O[k], W = exp(-+ 2 pi i / 2H).
+template <typename T, int H, bool INV> __device__ __forceinline__ void split2(cplx<T>* v, const cplx<T>* w) {
+  cplx<T> e[H], o[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    e[k] = v[2 * k];
+    o[k] = v[2 * k + 1];
+  }
+  Dft<T, H, INV>::run(e);
+  Dft<T, H, INV>::run(o);
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const cplx<T> t = c_mul<T>(o[k], w[k]);
+    v[k] = c_add<T>(e[k], t);
+    v[k + H] = c_sub<T>(e[k], t);
+  }
+}
+
+template <typename T, bool INV> struct Dft<T, 8, INV> {
+  __device__ __forceinline__ static void run(cplx<T>* v) {
+    const T r = T(0.70710678118654752440);
+    const T sg = INV ? T(1) : T(-1);
+    const cplx<T> w[4] = {mk<T>(T(1), T(0)), mk<T>(r, sg * r), mk<T>(T(0), sg), mk<T>(-r, sg * r)};
+    split2<T, 4, INV>(v, w);
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 16, INV> {
+  __device__ __forceinline__ static void run(cplx<T>* v) {
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r = T(0.70710678118654752440);
+    const T sg = INV ? T(1) : T(-1);
+    const cplx<T> w[8] = {mk<T>(T(1), T(0)), mk<T>(c1, sg * s1), mk<T>(r, sg * r), mk<T>(s1, sg * c1),
+                          mk<T>(T(0), sg),   mk<T>(-s1, sg * c1), mk<T>(-r, sg * r), mk<T>(-c1, sg * s1)};
+    split2<T, 8, INV>(v, w);
+  }
+};
+
+// One Stockham stage of radix R: each of the TPL lanes does RME / R butterflies.
+// FROM_REGS: inputs are v (stage 1 only, R == RME, positions j + TPL r).
+template <typename T, int RME, int R, bool INV, bool FROM_REGS>
+__device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, cplx<T>* v, int j,
+                                          int TPL, int L, int Ns, const cplx<T>* __restrict__ tw, int tws) {
+  const int step = L / R;
+#pragma unroll
+  for (int i = 0; i < RME / R; ++i) {
+    const int b = j + TPL * i;
+    const int k = b & (Ns - 1);
+    cplx<T> x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = FROM_REGS ? v[r] : src[spad(b + r * step)];
+    if (!FROM_REGS && Ns > 1) {
+      const int m1 = k * (L / (Ns * R)) * tws;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = __ldg(&tw[r * m1]);
+        if (INV) w.y = -w.y;
+        x[r] = c_mul<T>(x[r], w);
+      }
+    }
+    Dft<T, R, INV>::run(x);
+    const int base = (b - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[spad(base + r * Ns)] = x[r];
+  }
+}
+
+// FFT of one line; every thread of the block calls it with the same L (one barrier
+// per stage). v: the lane's RME inputs (positions j + TPL r). b0 / b1: the line's two
+// shared-memory buffers. Returns the buffer holding the natural-order result.
+template <typename T, int RM, bool INV>
+__device__ cplx<T>* line_fft(cplx<T>* v, int j, int L, cplx<T>* b0, cplx<T>* b1, const cplx<T>* __restrict__ tw,
+                             int tws) {
+  cplx<T>* cur = b0;
+  cplx<T>* nxt = b1;
+  int Ns;
+  if (L >= RM) {
+    const int TPL = L / RM;
+    fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, TPL, L, 1, tw, tws);
+    Ns = RM;
+  } else {
+    // one lane holds the whole line (TPL = 1, j = 0)
+    switch (L) {
+      case 2: fft_stage<T, 2, 2, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws); break;
+      case 4: fft_stage<T, 4, 4, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws); break;
+      case 8: fft_stage<T, 8, 8, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws); break;
+      default: break;
+    }
+    Ns = L;
+  }
+  __syncthreads();
+  const int TPL = L >= RM ? L / RM : 1;
+  while (Ns < L) {
+    const int rem = L / Ns;
+    if (rem >= RM) {
+      fft_stage<T, RM, RM, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws);
+      Ns *= RM;
+    } else {
+      switch (rem) {
+        case 2: fft_stage<T, RM, 2, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws); break;
+        case 4: fft_stage<T, RM, 4, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws); break;
+        case 8: fft_stage<T, RM, 8, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws); break;
+        default: break;
+      }
+      Ns = L;
+    }
+    cplx<T>* t = cur;
+    cur = nxt;
+    nxt = t;
+    __syncthreads();
+  }
+  return cur;
+}
+
+}  // namespace jfft

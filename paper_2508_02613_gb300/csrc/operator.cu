@@ -183,6 +183,120 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
   }
 }
 
+// 2D operator, warp-marching form (no shared memory, no block barriers). Lane l of
+// a warp owns node column c = c0 + l (mod n1, the contiguous axis) and walks `seg`
+// node rows along axis 0. Per element row e0 it holds the node values of rows e0
+// and e0 + 1 in registers, takes column c + 1 from lane l + 1 by a shuffle (lane 31
+// loads that halo column itself), computes the element whose lowest corner is
+// (e0, c), keeps the two corner forces of its own column and hands the two of
+// column c + 1 to lane l + 1 by a shuffle. Node (e0, c) is then complete for lanes
+// 1..31, so warps overlap by one column (stride 31): outputs o = 31 w + l, l >= 1.
+constexpr int kWarpStride = 31;
+constexpr int kWarpsPerCta2d = 4;
+
+template <typename T, int DOT, bool HAS_E>
+__global__ void __launch_bounds__(32 * kWarpsPerCta2d)
+    k_apply_K2d(Grid g, ElemConstT<T> ec, const T* __restrict__ E, T e_uniform, const T* __restrict__ x,
+                T* __restrict__ y, int64_t fstride, int seg, int groups, double* __restrict__ partial,
+                const CgState* __restrict__ cg) {
+  const int b = blockIdx.z;
+  if (cg && cg[b].done) return;
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int lane = threadIdx.x & 31;
+  const int grp = blockIdx.x * kWarpsPerCta2d + (threadIdx.x >> 5);
+  const bool active_warp = grp < groups;
+  const int o = grp * kWarpStride + lane;                  // output index before wrapping
+  const int c = o % n1, cr = (o + 1) % n1;                 // own column, halo column (lane 31)
+  const bool writer = active_warp && lane >= 1 && o <= n1;
+  const int ocol = o % n1;
+  const T* xb = x + (int64_t)b * fstride;
+  T* yb = y + (int64_t)b * fstride;
+  const int L0 = blockIdx.y * seg;
+  T dot = T(0);
+  if (active_warp) {
+    T lo[2], hi[2], rlo[2], rhi[2], carry[2];
+    T nx[2], nh[2];  // node row e0 + 2 (own column, halo column), loaded one step ahead
+    T En = T(0);     // element row e0 + 1, loaded one step ahead
+    {
+      const int row = (L0 - 1 + n0) % n0;
+      const int rown = L0 % n0;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        lo[a] = xb[a * g.N + (int64_t)row * n1 + c];
+        const T hlo = lane == 31 ? xb[a * g.N + (int64_t)row * n1 + cr] : T(0);
+        rlo[a] = __shfl_down_sync(0xffffffffu, lo[a], 1);
+        if (lane == 31) rlo[a] = hlo;
+        nx[a] = xb[a * g.N + (int64_t)rown * n1 + c];
+        nh[a] = lane == 31 ? xb[a * g.N + (int64_t)rown * n1 + cr] : T(0);
+        carry[a] = T(0);
+      }
+      if (HAS_E) En = E[(int64_t)row * n1 + c];
+    }
+    for (int e0 = L0 - 1; e0 < L0 + seg; ++e0) {
+      const T Ee = HAS_E ? En : e_uniform;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        hi[a] = nx[a];
+        rhi[a] = __shfl_down_sync(0xffffffffu, hi[a], 1);
+        if (lane == 31) rhi[a] = nh[a];
+      }
+      if (e0 + 1 < L0 + seg) {           // prefetch node row e0 + 2 and element row e0 + 1
+        const int rn2 = (e0 + 2) & (n0 - 1);   // n0 is a power of two
+        const int re1 = (e0 + 1) & (n0 - 1);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          nx[a] = xb[a * g.N + (int64_t)rn2 * n1 + c];
+          nh[a] = lane == 31 ? xb[a * g.N + (int64_t)rn2 * n1 + cr] : T(0);
+        }
+        if (HAS_E) En = E[(int64_t)re1 * n1 + c];
+      }
+      T u[2][4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        u[a][0] = lo[a];   // corner (0, 0): node (e0, c)
+        u[a][1] = rlo[a];  // corner (0, 1): node (e0, c + 1)
+        u[a][2] = hi[a];   // corner (1, 0): node (e0 + 1, c)
+        u[a][3] = rhi[a];  // corner (1, 1): node (e0 + 1, c + 1)
+      }
+      element_force<2, T, false>(ec, nullptr, u, Ee);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const T from_left_lo = __shfl_up_sync(0xffffffffu, u[a][1], 1);
+        const T from_left_hi = __shfl_up_sync(0xffffffffu, u[a][3], 1);
+        if (e0 >= L0 && writer) {
+          const T q = carry[a] + u[a][0] + from_left_lo;
+          yb[a * g.N + (int64_t)e0 * n1 + ocol] = q;
+          if (DOT == 1) dot += lo[a] * q;
+          if (DOT == 2) dot += q * q;
+        }
+        carry[a] = u[a][2] + from_left_hi;
+        lo[a] = hi[a];
+        rlo[a] = rhi[a];
+      }
+    }
+  }
+  if (DOT) {
+    const double s = block_sum((double)dot);
+    if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
+  }
+}
+
+template <typename T, int DOT, bool HAS_E>
+static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x, T* y, int nb,
+                               int64_t fstride, double* partial, int* nparts, const CgState* cg, cudaStream_t st) {
+  const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
+  const int ctas_x = (groups + kWarpsPerCta2d - 1) / kWarpsPerCta2d;
+  int seg = std::min(g.n[0], 16);
+  while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
+  dim3 grid(ctas_x, g.n[0] / seg, nb);
+  const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
+                                    : (DOT == 1 ? "apply_K" : (HAS_E ? "apply_K_plain" : "apply_K_ref"));
+  JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+                       g, ec, E, e_uniform, x, y, fstride, seg, groups, partial, cg));
+  if (nparts) *nparts = grid.x * grid.y;
+  return cudaGetLastError();
+}
+
 template <int D> static MarchGeom march_geom(const Grid& g) {
   MarchGeom m;
   if (D == 2) {
@@ -225,6 +339,11 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
                              double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, int dot_mode,
                              double* partial, int* nparts, const CgState* cg, cudaStream_t st) {
   const bool hx = x != nullptr, he = E != nullptr, sh = shifts != nullptr;
+  if (D == 2 && hx && !sh && sgn == 1.0 && dot_mode != 2) {
+    if (dot_mode == 1 && he) return apply_K2d_t<double, 1, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st);
+    if (dot_mode == 0 && he) return apply_K2d_t<double, 0, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st);
+    if (dot_mode == 0 && !he) return apply_K2d_t<double, 0, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st);
+  }
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
     return apply_K_t<double, D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st);
@@ -282,6 +401,10 @@ template <int D>
 static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, const float* E, const float* x, float* y,
                                  int nb, int64_t fstride, int dot_mode, double* partial, int* nparts, const CgState* cg,
                                  cudaStream_t st) {
+  if (D == 2) {
+    if (dot_mode == 1) return apply_K2d_t<float, 1, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st);
+    return apply_K2d_t<float, 0, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st);
+  }
   if (dot_mode == 1)
     return apply_K_t<float, D, 1, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
                                                     st);
