@@ -17,6 +17,16 @@ ifftn. With this convention (K u)_beta = F^-1( sum_alpha K_hat[alpha, beta] F(u_
 so the block acting on the vector of transformed components is K_hat^T; the
 oracle applies exactly that transpose (for the centrosymmetric Q1 stencil K_hat is
 real symmetric, so the transpose is immaterial, which a test asserts).
+
+Real, even symbol. The impulse response of the uniform reference operator is even
+in the node offset (the Q1 stencil is centrosymmetric), so its transform is the
+cosine sum K_hat(k) = sum_I R(I) cos(2 pi k.I / n): real, and equal at k and -k.
+A complex FFT of R returns that only up to rounding; the rounding-level imaginary
+and odd parts make F^-1 G_hat F slightly non-symmetric, and PCG with the
+Green-Jacobi preconditioner is sensitive to that (its iteration counts move by
+several at 256 x 256 and above). Step 2 therefore keeps the real part of the mean
+of the transform at k and at -k, which is the cosine sum above evaluated with the
+FFT, and the symbol is returned real.
 """
 
 from __future__ import annotations
@@ -59,13 +69,19 @@ def _transform(x, axes, inverse, explicit):
     return np.fft.ifftn(x, axes=axes) if inverse else np.fft.fftn(x, axes=axes)
 
 
+def _reflect(x: np.ndarray, axes) -> np.ndarray:
+    """x evaluated at -k on the periodic frequency grid (index k -> (n - k) mod n)."""
+    return np.roll(np.flip(x, axes), 1, axes)
+
+
 def green_symbol(n, C_ref: np.ndarray, explicit_dft: bool = False):
-    """Steps 2-3 of Alg. 1. Returns (K_hat, G_hat), each complex [d, d, *n]."""
+    """Steps 2-3 of Alg. 1. Returns (K_hat, G_hat), each real [d, d, *n]."""
     n = tuple(int(k) for k in n)
     d = len(n)
     R = impulse_responses(n, C_ref)
     axes = tuple(range(2, 2 + d))
-    K_hat = _transform(R, axes, False, explicit_dft)
+    K_c = _transform(R, axes, False, explicit_dft)
+    K_hat = 0.5 * (K_c + _reflect(K_c, axes)).real
     blocks = np.moveaxis(K_hat.reshape(d, d, -1), 2, 0)  # [N, d, d]
     G_blocks = np.zeros_like(blocks)
     G_blocks[1:] = np.linalg.inv(blocks[1:])  # frequency 0 is flat index 0

@@ -201,6 +201,24 @@ def test_small_workload_32x32(pc):
     assert rel(st, ref_t.stress[0]) <= 1e-9
 
 
+@pytest.mark.parametrize("contrast,pc", [(1e2, "green_jacobi"), (1e4, "green_jacobi"), (1e2, "green")])
+def test_iteration_counts_256_benchmark_density(contrast, pc):
+    """The benchmark's density recipe (16 modes, |k| <= 8, seed 0) at 256 x 256, three
+    Mandel loads batched, relative tolerance 1e-8: iteration counts within one of the
+    oracle's, true residual below the tolerance."""
+    shape = (256, 256)
+    rho = smooth_density(shape, 16, 8.0, 0)
+    E = material.young_from_density(rho, 1.0 / contrast, 1.0, 2.0)
+    s = _solver(shape, rho, contrast=contrast)
+    out = s.solve(mandel_unit_loads(2), 1e-8, pc, want_stress=False)
+    prob = osolve.setup(shape, E, 0.3)
+    for g in range(3):
+        f = assemble.assemble_rhs(shape, E, prob.C, np.eye(3)[g])
+        ref = pcg.pcg(prob.apply_K, prob.minv(pc), f, 1e-8, 100000)
+        assert abs(int(out["iters"][g]) - ref.iters) <= 1, (g, int(out["iters"][g]), ref.iters)
+        assert out["rel_res"][g] <= 1e-8 * 1.01
+
+
 @pytest.mark.parametrize("shape,normal,tangent", [((32, 8), [0, 2], [1]), ((16, 4, 4), [0, 4, 5], [1, 2, 3])])
 def test_laminate_closed_form(shape, normal, tangent):
     from tests.test_oracle_homogenisation import _laminate_C_hom

@@ -8,7 +8,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import assemble, fe, green, jacobi
+from oracle import assemble, fe, green, jacobi, material, solve
 from synthetic import random_field, smooth_density
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -108,6 +108,40 @@ def test_alg1_symbol_matches_closed_form(shape):
     assert np.abs(Kb @ Gb - np.eye(d)).max() < 1e-10
     # positive definite away from the zero frequency (Nyquist included)
     assert np.linalg.eigvalsh(Kb.real).min() > 0
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (16, 8), (4, 8, 4)])
+def test_alg1_transform_is_real_and_even_up_to_rounding(shape):
+    """The impulse response of the uniform Q1 operator is even in the node offset, so its
+    transform is real and even; the oracle's real, even symbol removes rounding only. A
+    wrong impulse position or a transposed response would leave O(1) imaginary parts."""
+    d = len(shape)
+    axes = tuple(range(2, 2 + d))
+    C = fe.C_unit(d, 0.3)
+    R = green.impulse_responses(shape, C)
+    K_c = np.fft.fftn(R, axes=axes)
+    scale = np.abs(R).sum(axis=axes).max()
+    assert np.abs(K_c.imag).max() <= 1e-14 * scale
+    reflected = np.roll(np.flip(K_c, axes), 1, axes)
+    assert np.abs(K_c - reflected).max() <= 1e-14 * scale
+    K_hat, G_hat = green.green_symbol(shape, C)
+    assert K_hat.dtype == np.float64 and G_hat.dtype == np.float64
+    assert np.abs(K_hat - K_c.real).max() <= 1e-14 * scale
+    assert np.array_equal(K_hat, np.roll(np.flip(K_hat, axes), 1, axes))
+
+
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+def test_preconditioners_are_symmetric(pc):
+    """M^-1 is symmetric (PCG's requirement): a . M b = b . M a for arbitrary fields."""
+    shape = (32, 16)
+    rho = smooth_density(shape, 16, 8.0, 0)
+    E = material.young_from_density(rho, 1e-3, 1.0, 2.0)
+    prob = solve.setup(shape, E, 0.3)
+    M = prob.minv(pc)
+    a = random_field((2,) + shape, 1)
+    b = random_field((2,) + shape, 2)
+    Mb, Ma = M(b), M(a)
+    assert abs(np.vdot(a, Mb) - np.vdot(b, Ma)) <= 1e-15 * np.linalg.norm(a) * np.linalg.norm(Mb) * 16
 
 
 def test_library_fft_equals_explicit_dft():
