@@ -31,7 +31,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cg_xr(typename V16<T>::t* __restrict__ x, typename V16<T>::t* __restrict__ r,
                                                const typename V16<T>::t* __restrict__ p,
                                                const typename V16<T>::t* __restrict__ q, int64_t n16, int64_t stride16,
-                                               const CgState* __restrict__ cg, double* __restrict__ partial) {
+                                               CgState* __restrict__ cg, double* __restrict__ partial, StageCtl sc) {
   using V = typename V16<T>::t;
   constexpr int NV = V16<T>::n;
   const int b = blockIdx.y;
@@ -66,24 +66,25 @@ __global__ void __launch_bounds__(256) k_cg_xr(typename V16<T>::t* __restrict__ 
   }
   const double sm = block_sum((double)acc);
   if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = sm;
+  fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x);
 }
 
 template <typename T>
 cudaError_t launch_cg_xr(const Grid& g, T* x, T* r, const T* p, const T* q, int nb, int64_t stride, CgState* cg,
-                         double* partial, int* nparts, cudaStream_t st) {
+                         double* partial, int* nparts, cudaStream_t st, StageCtl sc) {
   using V = typename V16<T>::t;
   const int64_t n16 = g.d * g.N / V16<T>::n;
   const int bl = vec16_blocks(n16);
   JFFT_K(nm<T>("cg_xr", "cg_xr_f32"), st,
          k_cg_xr<T><<<dim3(bl, nb), 256, 0, st>>>((V*)x, (V*)r, (const V*)p, (const V*)q, n16, stride / V16<T>::n,
-                                                  cg, partial));
+                                                  cg, partial, sc));
   *nparts = bl;
   return cudaGetLastError();
 }
 template cudaError_t launch_cg_xr<double>(const Grid&, double*, double*, const double*, const double*, int, int64_t,
-                                          CgState*, double*, int*, cudaStream_t);
+                                          CgState*, double*, int*, cudaStream_t, StageCtl);
 template cudaError_t launch_cg_xr<float>(const Grid&, float*, float*, const float*, const float*, int, int64_t,
-                                         CgState*, double*, int*, cudaStream_t);
+                                         CgState*, double*, int*, cudaStream_t, StageCtl);
 
 // p = z + beta p
 template <typename T>
@@ -129,8 +130,8 @@ template cudaError_t launch_cg_p<float>(const Grid&, float*, const float*, int, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__ r, T* __restrict__ z, int64_t stride,
                                                    const T* __restrict__ js, double3 jscale, double void_js,
-                                                   int identity, const CgState* __restrict__ cg,
-                                                   double* __restrict__ partial) {
+                                                   int identity, CgState* __restrict__ cg,
+                                                   double* __restrict__ partial, StageCtl sc) {
   const int b = blockIdx.y;
   if (cg && cg[b].done) return;
   const int64_t off = (int64_t)b * stride;
@@ -151,28 +152,29 @@ __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__
   }
   const double s = block_sum((double)acc);
   if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
+  fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x);
 }
 
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
                                   const double* jscale, double void_js, bool identity, double* partial, int* nparts,
-                                  const CgState* done, cudaStream_t st) {
+                                  CgState* done, cudaStream_t st, StageCtl sc) {
   const int bl = vec_blocks(g.d * g.N / 2);
   JFFT_K("jacobi_pc", st,
          k_jacobi_pc<double><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
                                                            make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                                           identity ? 1 : 0, done, partial));
+                                                           identity ? 1 : 0, done, partial, sc));
   *nparts = bl;
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
                                       const double* jscale, double void_js, bool identity, double* partial,
-                                      int* nparts, const CgState* done, cudaStream_t st) {
+                                      int* nparts, CgState* done, cudaStream_t st, StageCtl sc) {
   const int bl = vec_blocks(g.d * g.N / 2);
   JFFT_K("jacobi_pc_f32", st,
          k_jacobi_pc<float><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
                                                           make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                                          identity ? 1 : 0, done, partial));
+                                                          identity ? 1 : 0, done, partial, sc));
   *nparts = bl;
   return cudaGetLastError();
 }
@@ -180,7 +182,7 @@ cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, i
 // partial[b][blk] = sum a_b . c_b
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot(const T* __restrict__ a, const T* __restrict__ c, int64_t n,
-                                             int64_t stride, double* __restrict__ partial) {
+                                             int64_t stride, double* __restrict__ partial, CgState* cg, StageCtl sc) {
   const int b = blockIdx.y;
   const int64_t off = (int64_t)b * stride;
   T acc = T(0);
@@ -188,78 +190,36 @@ __global__ void __launch_bounds__(256) k_dot(const T* __restrict__ a, const T* _
     acc = fma(a[off + i], c[off + i], acc);
   const double s = block_sum((double)acc);
   if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
+  fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x);
 }
 
 template <typename T>
 cudaError_t launch_dot(const Grid& g, const T* a, const T* c, int nb, int64_t stride, double* partial, int* nparts,
-                       cudaStream_t st) {
+                       cudaStream_t st, CgState* cg, StageCtl sc) {
   const int bl = vec_blocks(g.d * g.N / 2);
-  JFFT_K(nm<T>("dot", "dot_f32"), st, k_dot<T><<<dim3(bl, nb), 256, 0, st>>>(a, c, g.d * g.N, stride, partial));
+  JFFT_K(nm<T>("dot", "dot_f32"), st, k_dot<T><<<dim3(bl, nb), 256, 0, st>>>(a, c, g.d * g.N, stride, partial, cg, sc));
   *nparts = bl;
   return cudaGetLastError();
 }
 template cudaError_t launch_dot<double>(const Grid&, const double*, const double*, int, int64_t, double*, int*,
-                                        cudaStream_t);
+                                        cudaStream_t, CgState*, StageCtl);
 template cudaError_t launch_dot<float>(const Grid&, const float*, const float*, int, int64_t, double*, int*,
-                                       cudaStream_t);
+                                       cudaStream_t, CgState*, StageCtl);
 
-// Scalar stages; one block per rhs.
-__global__ void __launch_bounds__(1024) k_scalars(int stage, CgState* __restrict__ cg, const double* __restrict__ partial,
-                                                  int nparts, double tol, int stop_mode, int max_iter) {
+// Scalar stages as a separate launch; one block per rhs (the same reduction order
+// and update as the fused tails of the producing kernels).
+__global__ void __launch_bounds__(256) k_scalars(int stage, CgState* __restrict__ cg, const double* __restrict__ partial,
+                                                 int nparts, double tol, int stop_mode, int max_iter) {
   const int b = blockIdx.x;
   CgState& s = cg[b];
   if (stage != kStageInitFF && s.done) return;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[(int64_t)b * kMaxPartials + i];
-  const double v = block_sum(acc);
-  if (threadIdx.x != 0) return;
-  switch (stage) {
-    case kStageInitFF: {
-      s.ff = v;
-      s.rr = v;
-      s.rr_stop = stop_mode == 0 ? tol * tol * v : tol;
-      s.iters = 0;
-      s.max_iter = max_iter;
-      s.alpha = 0.0;
-      s.beta = 0.0;
-      s.gamma = 0.0;
-      s.done = (v == 0.0 || v <= s.rr_stop) ? kConverged : kRunning;
-      if (!isfinite(v)) s.done = kBreakdown;
-      break;
-    }
-    case kStageInitGamma:
-      s.gamma = v;
-      s.beta = 0.0;
-      if (!(v > 0.0) || !isfinite(v)) s.done = kBreakdown;
-      break;
-    case kStageAlpha:
-      if (!(v > 0.0) || !isfinite(v)) {
-        s.done = kBreakdown;
-      } else {
-        s.alpha = s.gamma / v;
-      }
-      break;
-    case kStageRR:
-      s.rr = v;
-      s.iters += 1;
-      if (!isfinite(v)) s.done = kBreakdown;
-      else if (v <= s.rr_stop) s.done = kConverged;
-      else if (s.iters >= s.max_iter) s.done = kNoConv;
-      break;
-    case kStageBeta:
-      if (!isfinite(v)) {
-        s.done = kBreakdown;
-      } else {
-        s.beta = v / s.gamma;
-        s.gamma = v;
-      }
-      break;
-  }
+  const double v = canonical_sum(partial + (int64_t)b * kMaxPartials, nparts);
+  if (threadIdx.x == 0) apply_stage(s, stage, v, tol, stop_mode, max_iter);
 }
 
 cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,
                               int stop_mode, int max_iter, cudaStream_t st) {
-  JFFT_K("cg_scalars", st, k_scalars<<<nb, 1024, 0, st>>>(stage, cg, partial, nparts, tol, stop_mode, max_iter));
+  JFFT_K("cg_scalars", st, k_scalars<<<nb, 256, 0, st>>>(stage, cg, partial, nparts, tol, stop_mode, max_iter));
   return cudaGetLastError();
 }
 

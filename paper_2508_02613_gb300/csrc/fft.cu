@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __res
                                                   cplx<T>* __restrict__ cout, int R, int Lin, int lgTPL, int lgw,
                                                   const cplx<T>* __restrict__ tw, const T* __restrict__ js,
                                                   JScaleT<T> jsc, const T* __restrict__ rdot,
-                                                  double* __restrict__ partial, const CgState* __restrict__ cg,
-                                                  int slabs_per_b) {
+                                                  double* __restrict__ partial, CgState* __restrict__ cg,
+                                                  int slabs_per_b, StageCtl sc) {
   using C = cplx<T>;
   constexpr int RM = radix_max<T>();
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __res
     }
     const double s = block_sum((double)dot);
     if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + (int64_t)a * gridDim.x + blockIdx.x] = s;
+    fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, slabs_per_b * gridDim.x);
   } else {
 #pragma unroll
     for (int i = 0; i < RM; ++i) {
@@ -363,7 +364,7 @@ static cudaError_t pass_lines(const Grid& g, const FftPlanT<T>& p, int nb, bool 
 
 // 3D: complex inverse along axis 1, U[S'][n1][n0] -> T[S'][n0][n1].
 template <typename T>
-static cudaError_t pass_cols_cplx_inv(const Grid& g, const FftPlanT<T>& p, int nb, const CgState* cg, cudaStream_t st) {
+static cudaError_t pass_cols_cplx_inv(const Grid& g, const FftPlanT<T>& p, int nb, CgState* cg, cudaStream_t st) {
   const int R = g.n[0], Lin = g.n[1];
   const int w = rows_per_cta<T>(Lin, R);
   const size_t smem = (size_t)2 * w * line_slots(Lin) * sizeof(cplx<T>);
@@ -375,14 +376,14 @@ static cudaError_t pass_cols_cplx_inv(const Grid& g, const FftPlanT<T>& p, int n
   JScaleT<T> jsc = {};
   JFFT_K(nm<T>("fft_cols_cplx_inv", "fft_cols_cplx_inv_f32"), st,
          k<<<grid, w * tpl, smem, st>>>(g.d, p.U, nullptr, p.T, R, Lin, ilog2(tpl), ilog2(w), p.tw[1], nullptr, jsc, nullptr,
-                                        nullptr, cg, g.d * (g.M + 1)));
+                                        nullptr, cg, g.d * (g.M + 1), no_stage()));
   return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z, int nb, bool jac, const T* js,
                                       const JScaleT<T>& jsc, const T* r, double* partial, int* nparts,
-                                      const CgState* cg, cudaStream_t st) {
+                                      CgState* cg, cudaStream_t st, StageCtl sc) {
   const int n = g.n[g.d - 1];
   const int R = (int)(g.N / n);
   const int L = n / 2;
@@ -394,7 +395,7 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
   JFFT_TRY(set_smem(k, smem));
   JFFT_K(nm<T>("fft_cols_real_inv", "fft_cols_real_inv_f32"), st,
          k<<<grid, w * tpl, smem, st>>>(g.d, p.T, z, nullptr, R, L + 1, ilog2(tpl), ilog2(w), p.tw[g.d - 1], js, jsc, r,
-                                        partial, cg, g.d));
+                                        partial, cg, g.d, sc));
   if (nparts) *nparts = grid.x * g.d;
   return cudaGetLastError();
 }
@@ -402,7 +403,7 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
 template <typename T>
 static cudaError_t green_precond_t(const Grid& g, const FftPlanT<T>& p, const T* r, T* z, int nb, const T* js,
                                    const double* jscale, double void_js, bool jacobi, double* partial, int* nparts,
-                                   const CgState* done, cudaStream_t st) {
+                                   CgState* done, cudaStream_t st, StageCtl sc) {
   JScaleT<T> jsc;
   for (int a = 0; a < 3; ++a) jsc.k[a] = (T)jscale[a];
   jsc.void_js = (T)void_js;
@@ -410,19 +411,20 @@ static cudaError_t green_precond_t(const Grid& g, const FftPlanT<T>& p, const T*
   if (g.d == 3) JFFT_TRY(pass_rows_cplx_fwd<T>(g, p, nb, done, st));
   JFFT_TRY(pass_lines<T>(g, p, nb, true, done, st));
   if (g.d == 3) JFFT_TRY(pass_cols_cplx_inv<T>(g, p, nb, done, st));
-  return pass_cols_real_inv<T>(g, p, z, nb, jacobi, js, jsc, r, partial, nparts, done, st);
+  return pass_cols_real_inv<T>(g, p, z, nb, jacobi, js, jsc, r, partial, nparts, done, st, sc);
 }
 
 cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
                                  int64_t /*field_stride*/, const double* js, const double* jscale, double void_js,
-                                 bool jacobi, double* partial, int* nparts, const CgState* done, cudaStream_t st) {
-  return green_precond_t<double>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st);
+                                 bool jacobi, double* partial, int* nparts, CgState* done, cudaStream_t st,
+                                 StageCtl sc) {
+  return green_precond_t<double>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st, sc);
 }
 
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
                                      const float* js, const double* jscale, double void_js, bool jacobi,
-                                     double* partial, int* nparts, const CgState* done, cudaStream_t st) {
-  return green_precond_t<float>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st);
+                                     double* partial, int* nparts, CgState* done, cudaStream_t st, StageCtl sc) {
+  return green_precond_t<float>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st, sc);
 }
 
 cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,

@@ -37,6 +37,7 @@ struct jfft_solver {
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
   double *partial = nullptr, *red = nullptr;
   CgState* cg = nullptr;
+  unsigned* stage_cnt = nullptr;  // per-rhs arrival counters of the fused scalar stages
   StrainShift* shifts = nullptr;
   // FP32 copies and vectors of the mixed-precision inner solve
   int precision = JFFT_PREC_FP64;
@@ -400,7 +401,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   total += 5 * (size_t)nbmax * fe * sizeof(double);                 // x r p q z
   const size_t part_rows = (size_t)nbmax * 6;
   total += part_rows * kMaxPartials * sizeof(double);
-  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int));
+  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int) + sizeof(unsigned));
   if (o.precision == JFFT_PREC_MIXED) {
     total += 2 * g.N * sizeof(float) + (size_t)g.F * h->ds * sizeof(float);
     for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
@@ -434,6 +435,9 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->partial, part_rows * kMaxPartials * sizeof(double));
   AL(h->red, 1024 * sizeof(double));
   AL(h->cg, nbmax * sizeof(CgState));
+  AL(h->stage_cnt, nbmax * sizeof(unsigned));
+  ce = cudaMemset(h->stage_cnt, 0, nbmax * sizeof(unsigned));
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMemset"));
   AL(h->shifts, nbmax * sizeof(StrainShift));
   AL(h->active, nbmax * sizeof(int));
   if (o.precision == JFFT_PREC_MIXED) {
@@ -532,32 +536,33 @@ static Work<float> work32(jfft_solver* h) {
 }
 
 static cudaError_t apply_op(jfft_solver* h, const Work<double>& w, const double* x, double* y, int nb, int dot, int* np,
-                            const CgState* cg) {
-  return launch_apply_K(h->g, h->ec, w.E, 0.0, x, y, nb, field_elems(h), nullptr, 1.0, dot, h->partial, np, cg, h->st);
+                            CgState* cg, StageCtl sc = no_stage()) {
+  return launch_apply_K(h->g, h->ec, w.E, 0.0, x, y, nb, field_elems(h), nullptr, 1.0, dot, h->partial, np, cg, h->st,
+                        sc);
 }
 static cudaError_t apply_op(jfft_solver* h, const Work<float>& w, const float* x, float* y, int nb, int dot, int* np,
-                            const CgState* cg) {
-  return launch_apply_K_f32(h->g, h->ec, w.E, x, y, nb, field_elems(h), dot, h->partial, np, cg, h->st);
+                            CgState* cg, StageCtl sc = no_stage()) {
+  return launch_apply_K_f32(h->g, h->ec, w.E, x, y, nb, field_elems(h), dot, h->partial, np, cg, h->st, sc);
 }
 
 static cudaError_t precond_op(jfft_solver* h, const Work<double>& w, int pc, const double* r, double* z, int nb,
-                              const CgState* cg, int* np) {
+                              CgState* cg, int* np, StageCtl sc = no_stage()) {
   if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
     return launch_green_precond(h->g, w.pl, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js,
-                                pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st);
+                                pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st, sc);
   return launch_jacobi_precond(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
-                               h->partial, np, cg, h->st);
+                               h->partial, np, cg, h->st, sc);
 }
 static cudaError_t precond_op(jfft_solver* h, const Work<float>& w, int pc, const float* r, float* z, int nb,
-                              const CgState* cg, int* np) {
+                              CgState* cg, int* np, StageCtl sc = no_stage()) {
   if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
     return launch_green_precond_f32(h->g, w.pl, r, z, nb, w.js, h->jscale, h->void_js, pc == JFFT_PC_GREEN_JACOBI,
-                                    h->partial, np, cg, h->st);
+                                    h->partial, np, cg, h->st, sc);
   return launch_jacobi_precond_f32(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
-                                   h->partial, np, cg, h->st);
+                                   h->partial, np, cg, h->st, sc);
 }
 
-static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, int nb, const CgState* cg, int* np) {
+static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, int nb, CgState* cg, int* np) {
   CK(precond_op(h, work64(h), pc, r, z, nb, cg, np));
   return JFFT_OK;
 }
@@ -573,20 +578,19 @@ static jfft_status pcg_core_t(jfft_solver* h, const Work<T>& w, int nb, int pc, 
   jfft_status s;
   CK(cudaMemsetAsync(w.x, 0, nb * fe * sizeof(T), h->st));
   CK(cudaMemsetAsync(w.p, 0, nb * fe * sizeof(T), h->st));
-  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np));
-  CK(launch_cg_scalars(kStageInitGamma, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
+  CK(cudaMemsetAsync(h->stage_cnt, 0, nb * sizeof(unsigned), h->st));
+  // Each scalar stage runs in the last block of the kernel that produces its partials.
+  auto stage = [&](int k) { return StageCtl{k, stop_mode, h->max_iter, tol, h->stage_cnt}; };
+  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageInitGamma)));
   CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
   const int chunk = h->opt.check_every;
   int64_t launched = 0;
   const int64_t cap = (int64_t)h->max_iter + chunk;
   while (true) {
     for (int c = 0; c < chunk; ++c) {
-      CK(apply_op(h, w, w.p, w.q, nb, 1, &np, h->cg));
-      CK(launch_cg_scalars(kStageAlpha, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
-      CK(launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st));
-      CK(launch_cg_scalars(kStageRR, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
-      CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np));
-      CK(launch_cg_scalars(kStageBeta, h->cg, h->partial, np, nb, tol, stop_mode, h->max_iter, h->st));
+      CK(apply_op(h, w, w.p, w.q, nb, 1, &np, h->cg, stage(kStageAlpha)));
+      CK(launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st, stage(kStageRR)));
+      CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageBeta)));
       CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
     }
     launched += chunk;

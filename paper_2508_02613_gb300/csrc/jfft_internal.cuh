@@ -93,6 +93,18 @@ enum CgDone { kRunning = 0, kConverged = 1, kNoConv = 2, kBreakdown = 3 };
 // Reduction buffers: partial sums per (row, block), reduced in a fixed order.
 constexpr int kMaxPartials = 1 << 17;
 
+// A scalar stage fused into the kernel that produces its partial sums: the last
+// block to finish (per right-hand side, found with an atomic counter) reduces the
+// partials in a fixed order and applies the stage to CgState. stage < 0: none.
+struct StageCtl {
+  int stage;
+  int stop_mode;
+  int max_iter;
+  double tol;
+  unsigned* cnt;     // per-rhs arrival counters, zero between uses
+};
+inline StageCtl no_stage() { return StageCtl{-1, 0, 0, 0.0, nullptr}; }
+
 // Every kernel launch is bracketed by these hooks (launch counting and optional
 // CUDA-event timing per kernel name); implemented by the API layer.
 void hook_begin(const char* name, cudaStream_t st);
@@ -117,7 +129,7 @@ cudaError_t launch_check_field(const double* f, int64_t N, int* bad, cudaStream_
 // when cg != NULL and cg[b].done.
 cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
                            double* y, int nb, int64_t field_stride, const StrainShift* shifts, double sgn, int dot_mode,
-                           double* partial, int* nparts, const CgState* cg, cudaStream_t st);
+                           double* partial, int* nparts, CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
 
 // S3, one rhs, with a caller-supplied partial buffer of `cap` entries (see operator.cu).
 cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const double* E, const double* x, double* y,
@@ -125,8 +137,8 @@ cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const 
 
 // FP32 operator for the mixed-precision inner solve (no strain shift).
 cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* E, const float* x, float* y, int nb,
-                               int64_t field_stride, int dot_mode, double* partial, int* nparts, const CgState* cg,
-                               cudaStream_t st);
+                               int64_t field_stride, int dot_mode, double* partial, int* nparts, CgState* cg,
+                               cudaStream_t st, StageCtl sc = no_stage());
 
 // S8: element-averaged Mandel stress [nb][d*][N] (stress may be NULL) and partial
 // sums of vol * stress in partial[(b d* + s) * kMaxPartials + blk].
@@ -161,32 +173,34 @@ using FftPlan = FftPlanT<double>;
 // sums of r.z. jscale[a] = kappa_a^-1/2; void nodes use void_js.
 cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
                                  int64_t field_stride, const double* js, const double* jscale, double void_js,
-                                 bool jacobi, double* partial, int* nparts, const CgState* cg, cudaStream_t st);
+                                 bool jacobi, double* partial, int* nparts, CgState* cg, cudaStream_t st,
+                                 StageCtl sc = no_stage());
 // The same in FP32 (mixed-precision inner solve).
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
                                      const float* js, const double* jscale, double void_js, bool jacobi,
-                                     double* partial, int* nparts, const CgState* cg, cudaStream_t st);
+                                     double* partial, int* nparts, CgState* cg, cudaStream_t st,
+                                     StageCtl sc = no_stage());
 // Forward transform of nb d-component real fields -> line-major spectrum [nb][d][F].
 cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
                                     const double2** spec_out, cudaStream_t st);
 // z = J r (J = diag(K)^-1 with the void rule) or z = r (identity), partial r.z.
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
                                   const double* jscale, double void_js, bool identity, double* partial, int* nparts,
-                                  const CgState* cg, cudaStream_t st);
+                                  CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
 
 // S4: CG vector updates and inner products (T = double or float; scalars in FP64).
 template <typename T>
 cudaError_t launch_cg_xr(const Grid& g, T* x, T* r, const T* p, const T* q, int nb, int64_t stride, CgState* cg,
-                         double* partial, int* nparts, cudaStream_t st);
+                         double* partial, int* nparts, cudaStream_t st, StageCtl sc = no_stage());
 template <typename T>
 cudaError_t launch_cg_p(const Grid& g, T* p, const T* z, int nb, int64_t stride, CgState* cg, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dot(const Grid& g, const T* a, const T* c, int nb, int64_t stride, double* partial, int* nparts,
-                       cudaStream_t st);
+                       cudaStream_t st, CgState* cg = nullptr, StageCtl sc = no_stage());
 // FP32 variant of the Jacobi / identity preconditioner.
 cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
                                       const double* jscale, double void_js, bool identity, double* partial,
-                                      int* nparts, const CgState* cg, cudaStream_t st);
+                                      int* nparts, CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
 // Precision conversions for the refinement loop: dst = (float) src per rhs, zeroed
 // where active[b] == 0; u += (double) d; r = f - q with partial sums of r.r.
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n_per_rhs, int nb, const int* active, cudaStream_t st);

@@ -69,7 +69,8 @@ template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
 __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConstT<T> ec, const T* __restrict__ E,
                                                  T e_uniform, const T* __restrict__ x, T* __restrict__ y,
                                                  int64_t fstride, const StrainShift* __restrict__ shifts, T sgn,
-                                                 double* __restrict__ partial, const CgState* __restrict__ cg) {
+                                                 double* __restrict__ partial, CgState* __restrict__ cg,
+                                                 StageCtl sc) {
   constexpr int NC = 1 << D;
   constexpr int NCP = NC / 2;  // in-plane corners
   const int b = blockIdx.z;
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
   if (DOT) {
     const double s = block_sum((double)dot);
     if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
+    fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x * gridDim.y);
   }
 }
 
@@ -198,7 +200,7 @@ template <typename T, int DOT, bool HAS_E>
 __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
     k_apply_K2d(Grid g, ElemConstT<T> ec, const T* __restrict__ E, T e_uniform, const T* __restrict__ x,
                 T* __restrict__ y, int64_t fstride, int seg, int groups, double* __restrict__ partial,
-                const CgState* __restrict__ cg) {
+                CgState* __restrict__ cg, StageCtl sc) {
   const int b = blockIdx.z;
   if (cg && cg[b].done) return;
   const int n0 = g.n[0], n1 = g.n[1];
@@ -278,12 +280,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
   if (DOT) {
     const double s = block_sum((double)dot);
     if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
+    fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x * gridDim.y);
   }
 }
 
 template <typename T, int DOT, bool HAS_E>
 static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x, T* y, int nb,
-                               int64_t fstride, double* partial, int* nparts, const CgState* cg, cudaStream_t st) {
+                               int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
+                               StageCtl sc) {
   const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
   const int ctas_x = (groups + kWarpsPerCta2d - 1) / kWarpsPerCta2d;
   int seg = std::min(g.n[0], 16);
@@ -292,7 +296,7 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* 
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
                                     : (DOT == 1 ? "apply_K" : (HAS_E ? "apply_K_plain" : "apply_K_ref"));
   JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
-                       g, ec, E, e_uniform, x, y, fstride, seg, groups, partial, cg));
+                       g, ec, E, e_uniform, x, y, fstride, seg, groups, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
@@ -318,7 +322,7 @@ template <int D> static MarchGeom march_geom(const Grid& g) {
 template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
 static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x,
                              T* y, int nb, int64_t fstride, const StrainShift* shifts, T sgn, double* partial,
-                             int* nparts, const CgState* cg, cudaStream_t st) {
+                             int* nparts, CgState* cg, cudaStream_t st, StageCtl sc) {
   MarchGeom m = march_geom<D>(g);
   const size_t smem = march_smem<D, T>(m);
   auto kern = k_apply_K<T, D, DOT, HAS_X, HAS_E, SHIFT>;
@@ -329,7 +333,7 @@ static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const T* E,
   const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;
   const char* kname = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain") : DOT == 1 ? "apply_K"
                       : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
-  JFFT_K(kname, st, kern<<<grid, threads, smem, st>>>(g, m, ec, E, e_uniform, x, y, fstride, shifts, sgn, partial, cg));
+  JFFT_K(kname, st, kern<<<grid, threads, smem, st>>>(g, m, ec, E, e_uniform, x, y, fstride, shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
@@ -337,16 +341,16 @@ static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const T* E,
 template <int D>
 static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
                              double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, int dot_mode,
-                             double* partial, int* nparts, const CgState* cg, cudaStream_t st) {
+                             double* partial, int* nparts, CgState* cg, cudaStream_t st, StageCtl sc) {
   const bool hx = x != nullptr, he = E != nullptr, sh = shifts != nullptr;
   if (D == 2 && hx && !sh && sgn == 1.0 && dot_mode != 2) {
-    if (dot_mode == 1 && he) return apply_K2d_t<double, 1, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st);
-    if (dot_mode == 0 && he) return apply_K2d_t<double, 0, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st);
-    if (dot_mode == 0 && !he) return apply_K2d_t<double, 0, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st);
+    if (dot_mode == 1 && he) return apply_K2d_t<double, 1, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
+    if (dot_mode == 0 && he) return apply_K2d_t<double, 0, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
+    if (dot_mode == 0 && !he) return apply_K2d_t<double, 0, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
   }
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
-    return apply_K_t<double, D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st);
+    return apply_K_t<double, D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st, sc);
   JFFT_AK(1, true, true, false)   // CG: q = K p, p.q
   JFFT_AK(0, true, true, false)   // plain apply
   JFFT_AK(0, true, false, false)  // reference operator (uniform E)
@@ -360,10 +364,10 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
 
 cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
                            double* y, int nb, int64_t field_stride, const StrainShift* shifts, double sgn, int dot_mode,
-                           double* partial, int* nparts, const CgState* done, cudaStream_t st) {
+                           double* partial, int* nparts, CgState* done, cudaStream_t st, StageCtl sc) {
   if (g.d == 2)
-    return apply_K_d<2>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st);
-  return apply_K_d<3>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st);
+    return apply_K_d<2>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st, sc);
+  return apply_K_d<3>(g, ec, E, e_uniform, x, y, nb, field_stride, shifts, sgn, dot_mode, partial, nparts, done, st, sc);
 }
 
 // The CG operator variant (y = K x with per-CTA partial sums of x.y) for a caller
@@ -384,7 +388,7 @@ static cudaError_t apply_K_dot_capped_t(const Grid& g, const ElemConst& ec, cons
   dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, 1);
   const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;
   JFFT_K("apply_K_dot_capped", st,
-         kern<<<grid, threads, smem, st>>>(g, m, ec, E, 0.0, x, y, 0, nullptr, 1.0, partial, nullptr));
+         kern<<<grid, threads, smem, st>>>(g, m, ec, E, 0.0, x, y, 0, nullptr, 1.0, partial, nullptr, no_stage()));
   *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
@@ -399,25 +403,25 @@ cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const 
 // material in FP32, optional fused x.y partials (dot_mode 1) or none (0).
 template <int D>
 static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, const float* E, const float* x, float* y,
-                                 int nb, int64_t fstride, int dot_mode, double* partial, int* nparts, const CgState* cg,
-                                 cudaStream_t st) {
+                                 int nb, int64_t fstride, int dot_mode, double* partial, int* nparts, CgState* cg,
+                                 cudaStream_t st, StageCtl sc) {
   if (D == 2) {
-    if (dot_mode == 1) return apply_K2d_t<float, 1, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st);
-    return apply_K2d_t<float, 0, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st);
+    if (dot_mode == 1) return apply_K2d_t<float, 1, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
+    return apply_K2d_t<float, 0, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
   }
   if (dot_mode == 1)
     return apply_K_t<float, D, 1, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
-                                                    st);
+                                                    st, sc);
   return apply_K_t<float, D, 0, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
-                                                  st);
+                                                  st, sc);
 }
 
 cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* E, const float* x, float* y, int nb,
-                               int64_t field_stride, int dot_mode, double* partial, int* nparts, const CgState* cg,
-                               cudaStream_t st) {
+                               int64_t field_stride, int dot_mode, double* partial, int* nparts, CgState* cg,
+                               cudaStream_t st, StageCtl sc) {
   const ElemConstT<float> ecf = elem_const_as<float>(ec);
-  if (g.d == 2) return apply_K_f32_d<2>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st);
-  return apply_K_f32_d<3>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st);
+  if (g.d == 2) return apply_K_f32_d<2>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st, sc);
+  return apply_K_f32_d<3>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st, sc);
 }
 
 // ------------------------------------------------------------------ S8
