@@ -43,7 +43,18 @@ template <typename T, bool INV> __device__ __forceinline__ cplx<T> twmul(cplx<T>
   return mk<T>(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
 }
 
-template <typename T> constexpr int radix_max() { return sizeof(T) == 4 ? 16 : 8; }
+// Largest radix of the engine per precision, and the launch shape of the passes:
+// threads per row / column block and the minimum resident blocks per SM they are
+// compiled for (register budget). FP32 runs radix 8 at 64 registers (four
+// 256-thread blocks per SM); radix 16 needs ~128 registers, halves the resident
+// warps and measured slower on GB300.
+template <typename T> struct FftOcc {
+  static constexpr int radix = sizeof(T) == 4 ? 8 : 8;
+  static constexpr int rows_threads = 256;
+  static constexpr int rows = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int lines = sizeof(T) == 4 ? 2 : 1;
+};
+template <typename T> constexpr int radix_max() { return FftOcc<T>::radix; }
 
 // Threads per line for the engine.
 template <typename T> __host__ __device__ inline int lanes_per_line(int L) {
@@ -67,7 +78,7 @@ template <typename T> __device__ __forceinline__ T jhalf(const T* __restrict__ j
 // in: [S][R][Lin] (real or complex); out: [S][Lout][R]. w rows per block, TPL lanes
 // per row (block = w * TPL threads).
 template <typename T, bool REAL, bool JAC>
-__global__ void __launch_bounds__(256, 2) k_rows_fwd(int D, const T* __restrict__ rin, const cplx<T>* __restrict__ cin,
+__global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_rows_fwd(int D, const T* __restrict__ rin, const cplx<T>* __restrict__ cin,
                                                   cplx<T>* __restrict__ out, int R, int Lin, int lgTPL, int lgw,
                                                   const cplx<T>* __restrict__ tw, const T* __restrict__ js,
                                                   JScaleT<T> jsc, const CgState* __restrict__ cg, int slabs_per_b) {
@@ -85,8 +96,12 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd(int D, const T* __restrict_
   const int TPL = 1 << lgTPL;
   const int RME = L < RM ? L : RM;
   const int line = threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
-  C* A = sm2;
-  C* B = sm2 + w * ls;
+  // twiddle table of the axis (Lin entries) in shared memory; the engine's first
+  // barrier orders these stores before any use
+  C* twl = sm2;
+  for (int i = threadIdx.x; i < Lin; i += blockDim.x) twl[i] = tw[i];
+  C* A = sm2 + Lin;
+  C* B = A + w * ls;
   T ka = T(0);
   if (JAC) ka = kscale<T>(jsc, S % D);
   const int64_t row = r0 + line;
@@ -109,7 +124,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd(int D, const T* __restrict_
       v[r] = x;
     }
   }
-  C* res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, tw, REAL ? 2 : 1);
+  C* res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, twl, REAL ? 2 : 1);
   res -= line * ls;  // back to the block's buffer base
   if (REAL) {
     // X[k] = (Z[k] + conj Z[M-k]) - i W^k (Z[k] - conj Z[M-k]), k = 0..M (times 2);
@@ -119,7 +134,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd(int D, const T* __restrict_
       const C zk = z[spad(k)], zm = z[spad((L - k) & (L - 1))];
       const C A_ = mk<T>(zk.x + zm.x, zk.y - zm.y);
       const C B_ = mk<T>(zk.x - zm.x, zk.y + zm.y);
-      const C Cw = twmul<T, false>(B_, tw[k]);
+      const C Cw = twmul<T, false>(B_, twl[k]);
       z[spad(k)] = mk<T>(A_.x + Cw.y, A_.y - Cw.x);
       z[spad(L - k)] = mk<T>(A_.x - Cw.y, -A_.y - Cw.x);
     }
@@ -135,7 +150,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd(int D, const T* __restrict_
 // forward FFT, block multiply by the stored symbol, inverse FFT (or forward only).
 // Block = D * TPL threads; lanes [a TPL, (a+1) TPL) transform component a.
 template <typename T, int D, bool GREEN>
-__global__ void __launch_bounds__(512, 1) k_lines(cplx<T>* __restrict__ spec, int nlines, int L, int lgTPL,
+__global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __restrict__ spec, int nlines, int L, int lgTPL,
                                                const cplx<T>* __restrict__ tw, const T* __restrict__ G,
                                                const CgState* __restrict__ cg) {
   using C = cplx<T>;
@@ -149,14 +164,16 @@ __global__ void __launch_bounds__(512, 1) k_lines(cplx<T>* __restrict__ spec, in
   const int TPL = 1 << lgTPL;
   const int RME = L < RM ? L : RM;
   const int a = threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
-  C* A = sm2;
-  C* B = sm2 + D * ls;
+  C* twl = sm2;  // twiddle table (L entries), ordered by the engine's first barrier
+  for (int i = threadIdx.x; i < L; i += blockDim.x) twl[i] = tw[i];
+  C* A = sm2 + L;
+  C* B = A + D * ls;
   const C* gline = spec + (((int64_t)b * D + a) * nlines + l) * L;
   C v[RM];
 #pragma unroll
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = gline[j + TPL * r];
-  C* res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, tw, 1) - a * ls;
+  C* res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, twl, 1) - a * ls;
   if (GREEN) {
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
       const T* gk = G + ((int64_t)l * L + k) * NCMP;
@@ -185,7 +202,7 @@ __global__ void __launch_bounds__(512, 1) k_lines(cplx<T>* __restrict__ spec, in
       if (r < RME) v[r] = res[a * ls + spad(j + TPL * r)];
     C* other = (res == A) ? B : A;
     // stage 1 writes `other` first, so no lane overwrites values still being read from res
-    res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, tw, 1) - a * ls;
+    res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, twl, 1) - a * ls;
   }
   C* gout = spec + (((int64_t)b * D + a) * nlines + l) * L;
 #pragma unroll
@@ -200,7 +217,7 @@ __global__ void __launch_bounds__(512, 1) k_lines(cplx<T>* __restrict__ spec, in
 // in: [S][Lin][R]; out: [S][R][Lout] (real: Lout = 2 (Lin - 1), with J^1/2 and the
 // r . z partial; complex: Lout = Lin). w rows per block, TPL lanes per row.
 template <typename T, bool REAL, bool JAC>
-__global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __restrict__ in, T* __restrict__ rout,
+__global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_cols_inv(int D, const cplx<T>* __restrict__ in, T* __restrict__ rout,
                                                   cplx<T>* __restrict__ cout, int R, int Lin, int lgTPL, int lgw,
                                                   const cplx<T>* __restrict__ tw, const T* __restrict__ js,
                                                   JScaleT<T> jsc, const T* __restrict__ rdot,
@@ -220,8 +237,11 @@ __global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __res
   const int TPL = 1 << lgTPL;
   const int RME = L < RM ? L : RM;
   const int line = threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
-  C* A = sm2;
-  C* B = sm2 + w * ls;
+  const int ntw = REAL ? 2 * L : L;  // twiddle table of the axis in shared memory
+  C* twl = sm2;
+  for (int i = threadIdx.x; i < ntw; i += blockDim.x) twl[i] = tw[i];
+  C* A = sm2 + ntw;
+  C* B = A + w * ls;
   for (int t = threadIdx.x; t < w * Lin; t += blockDim.x) {
     const int k = t >> lgw, ln = t & (w - 1);
     A[ln * ls + spad(k)] = in[((int64_t)S * Lin + k) * R + r0 + ln];
@@ -236,7 +256,7 @@ __global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __res
       if (k == 0) { xk.y = T(0); xm.y = T(0); }
       const C E = mk<T>(xk.x + xm.x, xk.y - xm.y);
       const C Bv = mk<T>(xk.x - xm.x, xk.y + xm.y);
-      const C O = twmul<T, true>(Bv, tw[k]);
+      const C O = twmul<T, true>(Bv, twl[k]);
       x[spad(k)] = mk<T>(E.x - O.y, E.y + O.x);
       if (k != 0) x[spad(L - k)] = mk<T>(E.x + O.y, -E.y + O.x);
     }
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __res
 #pragma unroll
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = A[line * ls + spad(j + TPL * r)];
-  C* res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, tw, REAL ? 2 : 1) - line * ls;
+  C* res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, twl, REAL ? 2 : 1) - line * ls;
   if (REAL) {
     T dot = T(0);
     const int n = 2 * L;
@@ -284,14 +304,18 @@ __global__ void __launch_bounds__(256, 2) k_cols_inv(int D, const cplx<T>* __res
 
 static int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
-// Lines per block for the row / column passes: up to 256 threads and ~96 KB of
-// shared memory (two buffers of w lines), never more lines than there are rows.
-template <typename T> static int rows_per_cta(int L, int R) {
+// Lines per block for the row / column passes: up to FftOcc<T>::rows_threads
+// threads and ~96 KB of shared memory (two buffers of w lines plus the ntw-entry
+// twiddle table), never more lines than there are rows.
+template <typename T> static int rows_per_cta(int L, int R, int ntw) {
   const int tpl = lanes_per_line<T>(L);
-  int w = std::max(1, 256 / tpl);
-  while (w > 1 && (size_t)2 * w * line_slots(L) * sizeof(cplx<T>) > 98304) w >>= 1;
+  int w = std::max(1, FftOcc<T>::rows_threads / tpl);
+  while (w > 1 && ((size_t)2 * w * line_slots(L) + ntw) * sizeof(cplx<T>) > 98304) w >>= 1;
   while (w > R) w >>= 1;
   return w;
+}
+template <typename T> static size_t rows_smem(int L, int w, int ntw) {
+  return ((size_t)2 * w * line_slots(L) + ntw) * sizeof(cplx<T>);
 }
 
 template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
@@ -311,8 +335,8 @@ static cudaError_t pass_rows_real_fwd(const Grid& g, const FftPlanT<T>& p, const
   const int Lin = g.n[g.d - 1];
   const int R = (int)(g.N / Lin);
   const int L = Lin / 2;
-  const int w = rows_per_cta<T>(L, R);
-  const size_t smem = (size_t)2 * w * line_slots(L) * sizeof(cplx<T>);
+  const int w = rows_per_cta<T>(L, R, Lin);
+  const size_t smem = rows_smem<T>(L, w, Lin);
   dim3 grid(R / w, nb * g.d);
   const int tpl = lanes_per_line<T>(L);
   auto k = jac ? k_rows_fwd<T, true, true> : k_rows_fwd<T, true, false>;
@@ -326,8 +350,8 @@ static cudaError_t pass_rows_real_fwd(const Grid& g, const FftPlanT<T>& p, const
 template <typename T>
 static cudaError_t pass_rows_cplx_fwd(const Grid& g, const FftPlanT<T>& p, int nb, const CgState* cg, cudaStream_t st) {
   const int R = g.n[0], Lin = g.n[1];
-  const int w = rows_per_cta<T>(Lin, R);
-  const size_t smem = (size_t)2 * w * line_slots(Lin) * sizeof(cplx<T>);
+  const int w = rows_per_cta<T>(Lin, R, Lin);
+  const size_t smem = rows_smem<T>(Lin, w, Lin);
   const int slabs = nb * g.d * (g.M + 1);
   dim3 grid(R / w, slabs);
   const int tpl = lanes_per_line<T>(Lin);
@@ -346,7 +370,7 @@ static cudaError_t pass_lines(const Grid& g, const FftPlanT<T>& p, int nb, bool 
   const int L = g.n[0];
   const int nlines = (int)(g.F / L);
   cplx<T>* spec = (g.d == 2) ? p.T : p.U;
-  const size_t smem = (size_t)2 * g.d * line_slots(L) * sizeof(cplx<T>);
+  const size_t smem = ((size_t)2 * g.d * line_slots(L) + L) * sizeof(cplx<T>);
   const int tpl = lanes_per_line<T>(L);
   dim3 grid(nlines, nb);
   const char* name = green ? nm<T>("fft_lines", "fft_lines_f32") : nm<T>("fft_lines_fwd", "fft_lines_fwd_f32");
@@ -366,8 +390,8 @@ static cudaError_t pass_lines(const Grid& g, const FftPlanT<T>& p, int nb, bool 
 template <typename T>
 static cudaError_t pass_cols_cplx_inv(const Grid& g, const FftPlanT<T>& p, int nb, CgState* cg, cudaStream_t st) {
   const int R = g.n[0], Lin = g.n[1];
-  const int w = rows_per_cta<T>(Lin, R);
-  const size_t smem = (size_t)2 * w * line_slots(Lin) * sizeof(cplx<T>);
+  const int w = rows_per_cta<T>(Lin, R, Lin);
+  const size_t smem = rows_smem<T>(Lin, w, Lin);
   const int slabs = nb * g.d * (g.M + 1);
   dim3 grid(R / w, slabs);
   const int tpl = lanes_per_line<T>(Lin);
@@ -387,8 +411,8 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
   const int n = g.n[g.d - 1];
   const int R = (int)(g.N / n);
   const int L = n / 2;
-  const int w = rows_per_cta<T>(L, R);
-  const size_t smem = (size_t)2 * w * line_slots(L) * sizeof(cplx<T>);
+  const int w = rows_per_cta<T>(L, R, n);
+  const size_t smem = rows_smem<T>(L, w, n);
   dim3 grid(R / w, nb * g.d);
   const int tpl = lanes_per_line<T>(L);
   auto k = jac ? k_cols_inv<T, true, true> : k_cols_inv<T, true, false>;

@@ -98,6 +98,7 @@ template <typename T, bool INV> struct Dft<T, 16, INV> {
 
 // One Stockham stage of radix R: each of the TPL lanes does RME / R butterflies.
 // FROM_REGS: inputs are v (stage 1 only, R == RME, positions j + TPL r).
+// tw: twiddle table exp(-2 pi i m / (L tws)) in shared memory (read with plain loads).
 template <typename T, int RME, int R, bool INV, bool FROM_REGS>
 __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, cplx<T>* v, int j,
                                           int TPL, int L, int Ns, const cplx<T>* __restrict__ tw, int tws) {
@@ -113,7 +114,7 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
       const int m1 = k * (L / (Ns * R)) * tws;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cplx<T> w = __ldg(&tw[r * m1]);
+        cplx<T> w = tw[r * m1];  // tw is the block's shared-memory copy of the table
         if (INV) w.y = -w.y;
         x[r] = c_mul<T>(x[r], w);
       }
