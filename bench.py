@@ -374,8 +374,8 @@ def main():
         barrier()
         clocks = ClockSampler(smi_id)
         clocks.start()
-        s.set_profiling(True)
         n0 = s.launch_count
+        r0 = s.graph_replays
         times = []
         for _ in range(args.steps):
             flush.fill_(1.0)   # L2 flush (256 MiB > 129 MB L2), outside the timed interval
@@ -387,17 +387,34 @@ def main():
             barrier()
             times.append(e0.elapsed_time(e1))
         launches = s.launch_count - n0
+        replays = s.graph_replays - r0
+        clk = clocks.stop()
+        # Per-kernel durations: the same steps again with a CUDA event pair around every
+        # kernel launch (the PCG chunk then runs as a replayed graph with event nodes
+        # instead of the device-side loop, which cannot hold event nodes).
+        s.set_profiling(True)
+        prof_times = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            barrier()
+            prof_times.append(e0.elapsed_time(e1))
         prof = s.profile()
         s.set_profiling(False)
-        clk = clocks.stop()
         s.close()
         ms, value = aggregate(statistics.mean(times), world, solves_per_step, dist, "cuda")
         return {"ms": ms, "value": value, "times": times, "rec": rec, "prof": prof, "launches": launches,
+                "graph_replays": replays, "profiled_step_ms": prof_times,
                 "clocks": clk}
 
     def roofline(leg, alu):
-        """Dominant kernel of the timed region with its achieved rate. Units are right-hand-
-        side applications: per load, one operator and one preconditioner per PCG iteration."""
+        """Dominant kernel with its achieved rate, from the per-kernel CUDA events of the
+        profiling pass that repeats the timed steps. Units are right-hand-side applications:
+        per load, one operator and one preconditioner per PCG iteration."""
         n_units = sum(sum(r["iters"]) for r in leg["rec"].values()) * args.steps
         rows = sorted(((k, v[0], v[1]) for k, v in leg["prof"].items()), key=lambda r: -r[2])
         total_ms = sum(r[2] for r in rows)
@@ -473,6 +490,8 @@ def main():
         "refine_steps": {f"{pc}@{c:g}": v["refine"] for (c, pc), v in mixed["rec"].items()},
         "rel_res_max": max(max(v["rel_res"]) for v in mixed["rec"].values()),
         "kernels_ms_total": {k: round(v[1], 3) for k, v in mixed["prof"].items()},
+        "graph_replays": mixed["graph_replays"],
+        "profiled_step_ms": mixed["profiled_step_ms"],
     }
     clk = fp64["clocks"]
     times = fp64["times"]
@@ -502,6 +521,8 @@ def main():
                        "rel_res_max": max(max(v["rel_res"]) for v in fp64["rec"].values()),
                        "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()},
                        "kernel_launches": {k: v[0] for k, v in prof.items()},
+                       "graph_replays": fp64["graph_replays"],
+                       "profiled_step_ms": fp64["profiled_step_ms"],
                        "step_ms": times},
         }
         print(json.dumps(line), flush=True)

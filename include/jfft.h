@@ -106,7 +106,8 @@ typedef struct {
   int precision;             /* jfft_precision (FP64) */
   int max_iter;              /* PCG iteration cap per load case (default 100000) */
   int stop_mode;             /* jfft_stop_mode (default JFFT_STOP_REL) */
-  void* stream;              /* cudaStream_t to run on; NULL = the legacy default stream */
+  void* stream;              /* cudaStream_t to run on; NULL = a stream the solver creates, ordered
+                                after earlier and before later work on the legacy default stream */
   size_t hbm_budget;         /* bytes the workspace may take; 0 = no limit beyond free memory */
   int check_every;           /* PCG iterations launched between host convergence checks (default 8) */
   int io_memory;             /* jfft_memory for the data pointers of later calls (default HOST) */
@@ -115,6 +116,9 @@ typedef struct {
   int device;                /* CUDA device ordinal (default 0) */
   double inner_tol;          /* MIXED: relative residual of each FP32 inner solve (default 1e-3) */
   int max_refine;            /* MIXED: largest number of inner solves per load (default 30) */
+  int graphs;                /* 1 (default): the check_every-iteration PCG chunk is captured once as a
+                                CUDA graph and replayed; 0: every kernel is launched from the host.
+                                Results are identical; graphs are not used while profiling is on. */
 } jfft_options;
 
 typedef struct {
@@ -248,8 +252,12 @@ jfft_status jfft_apply_K_dot_noalloc(const jfft_grid* grid, double nu, const dou
 
 /* ---- instrumentation ---- */
 
-/* Number of kernels this handle has launched since creation. */
+/* Number of kernels this handle has launched since creation (kernels inside a
+ * replayed CUDA graph count once per replay). */
 int64_t jfft_launch_count(const jfft_solver* h);
+
+/* Number of PCG chunks this handle has run as a CUDA graph replay (options.graphs). */
+int64_t jfft_graph_replays(const jfft_solver* h);
 
 /* When on, every kernel launch is bracketed by CUDA events on the handle's stream
  * and accumulated per kernel name; jfft_profile_json returns

@@ -206,6 +206,25 @@ template cudaError_t launch_dot<double>(const Grid&, const double*, const double
 template cudaError_t launch_dot<float>(const Grid&, const float*, const float*, int, int64_t, double*, int*,
                                        cudaStream_t, CgState*, StageCtl);
 
+// Loop condition of the device-side PCG loop (a CUDA graph WHILE node whose body is
+// one chunk of iterations): counts the chunk and continues while any right-hand
+// side is running and fewer than cap chunks have run.
+__global__ void k_cg_continue(const CgState* __restrict__ cg, int nb, int* __restrict__ chunks, int cap,
+                              cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0) return;
+  const int n = chunks[0] + 1;
+  chunks[0] = n;
+  bool running = false;
+  for (int b = 0; b < nb; ++b) running = running || cg[b].done == kRunning;
+  cudaGraphSetConditional(cond, (running && n < cap) ? 1u : 0u);
+}
+
+cudaError_t launch_cg_continue(const CgState* cg, int nb, int* chunks, int cap, cudaGraphConditionalHandle cond,
+                               cudaStream_t st) {
+  JFFT_K("cg_continue", st, k_cg_continue<<<1, 32, 0, st>>>(cg, nb, chunks, cap, cond));
+  return cudaGetLastError();
+}
+
 // Scalar stages as a separate launch; one block per rhs (the same reduction order
 // and update as the fused tails of the producing kernels).
 __global__ void __launch_bounds__(256) k_scalars(int stage, CgState* __restrict__ cg, const double* __restrict__ partial,

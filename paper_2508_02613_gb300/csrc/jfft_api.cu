@@ -60,6 +60,35 @@ struct jfft_solver {
   std::vector<cudaEvent_t> pool;
   std::map<std::string, std::pair<int64_t, double>> prof;
   std::string prof_json;
+  // own stream (options.stream == NULL), ordered against the legacy default stream
+  bool own_stream = false;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // CUDA graph of one check_every-iteration PCG chunk, per working precision
+  struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    int nb = -1, pc = -1, stop_mode = -1, max_iter = -1, chunk = -1;
+    double tol = -1.0;
+    int64_t launches = 0;
+    bool prof = false;         // captured with per-kernel timing events
+    std::vector<Pend> events;  // those events, re-recorded by every replay
+  };
+  ChunkGraph graph[2];
+  ChunkGraph* replayed = nullptr;  // graph whose events the next sync reads
+  // CUDA graph of a whole PCG solve: a WHILE node around one chunk, ended on the
+  // device when every right-hand side is done (no host polling), per precision
+  struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+    int nb = -1, pc = -1, stop_mode = -1, max_iter = -1, chunk = -1;
+    double tol = -1.0;
+    int64_t launches_per_chunk = 0;
+  };
+  LoopGraph loop[2];
+  bool loop_ok = true;      // cleared if the loop graph cannot be built here
+  int* chunks_d = nullptr;  // chunks run by the last device-side loop
+  int* chunks_h = nullptr;
+  bool graphs_ok = true;  // cleared if a capture fails; kernels are then launched directly
+  bool capturing = false;
+  int64_t graph_replays = 0;
 };
 
 // ------------------------------------------------------------- launch hooks
@@ -80,23 +109,58 @@ void hook_begin(const char* name, cudaStream_t st) {
     else cudaEventCreate(&ev);
     (i == 0 ? pe.a : pe.b) = ev;
   }
-  cudaEventRecord(pe.a, st);
+  // inside a graph capture the record must be an event-record node (External),
+  // not a capture-internal dependency, so that the replay's timing can be read
+  cudaEventRecordWithFlags(pe.a, st, h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   h->pend.push_back(pe);
 }
 void hook_end(const char* /*name*/, cudaStream_t st) {
   jfft_solver* h = g_cur;
   if (!h || !h->profiling || h->pend.empty()) return;
-  cudaEventRecord(h->pend.back().b, st);
+  cudaEventRecordWithFlags(h->pend.back().b, st, h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 }  // namespace jfft
 
+// Per-call scope: selects the solver and device; for a solver on its own stream,
+// orders the call after earlier legacy-stream work and later legacy-stream work
+// after the call.
 struct CurGuard {
   jfft_solver* prev;
-  explicit CurGuard(jfft_solver* h) : prev(g_cur) { g_cur = h; if (h) cudaSetDevice(h->device); }
-  ~CurGuard() { g_cur = prev; }
+  jfft_solver* cur;
+  explicit CurGuard(jfft_solver* h) : prev(g_cur), cur(h) {
+    g_cur = h;
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->own_stream) {
+      cudaEventRecord(h->ev_in, cudaStreamLegacy);
+      cudaStreamWaitEvent(h->st, h->ev_in, 0);
+    }
+  }
+  ~CurGuard() {
+    if (cur && cur->own_stream) {
+      cudaEventRecord(cur->ev_out, cur->st);
+      cudaStreamWaitEvent(cudaStreamLegacy, cur->ev_out, 0);
+    }
+    g_cur = prev;
+  }
 };
 
+static void accumulate(jfft_solver* h, const jfft_solver::Pend& pe) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+    auto& e = h->prof[pe.name];
+    e.first += 1;
+    e.second += ms;
+  } else {
+    cudaGetLastError();  // a timing that cannot be read is dropped, not reported as a failure
+  }
+}
+
 static void drain_profile(jfft_solver* h) {
+  if (h->replayed) {
+    for (auto& pe : h->replayed->events) accumulate(h, pe);
+    h->replayed = nullptr;
+  }
   for (auto& pe : h->pend) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
@@ -133,7 +197,19 @@ static jfft_status sync(jfft_solver* h) {
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   if (h->profiling) drain_profile(h);
+  h->replayed = nullptr;
   return JFFT_OK;
+}
+
+static void drop_graph(jfft_solver* h, jfft_solver::ChunkGraph& gr) {
+  if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  gr.exec = nullptr;
+  for (auto& pe : gr.events) {
+    h->pool.push_back(pe.a);
+    h->pool.push_back(pe.b);
+  }
+  gr.events.clear();
+  if (h->replayed == &gr) h->replayed = nullptr;
 }
 
 static int64_t field_elems(const jfft_solver* h) { return (int64_t)h->g.d * h->g.N; }
@@ -174,6 +250,7 @@ extern "C" void jfft_default_options(jfft_options* o) {
   o->device = 0;
   o->inner_tol = 1e-3;
   o->max_refine = 30;
+  o->graphs = 1;
 }
 
 static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
@@ -195,10 +272,26 @@ static void free_all(jfft_solver* h) {
   h->cg_h = nullptr;
   h->red_h = nullptr;
   h->active_h = nullptr;
+  for (auto& gr : h->graph) drop_graph(h, gr);
+  for (auto& lg : h->loop)
+    if (lg.exec) {
+      cudaGraphExecDestroy(lg.exec);
+      lg.exec = nullptr;
+    }
+  if (h->chunks_h) cudaFreeHost(h->chunks_h);
+  h->chunks_h = nullptr;
   for (auto& pe : h->pend) { h->pool.push_back(pe.a); h->pool.push_back(pe.b); }
   for (auto ev : h->pool) cudaEventDestroy(ev);
   h->pool.clear();
   h->pend.clear();
+  if (h->own_stream) {
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    cudaStreamDestroy(h->st);
+    h->ev_in = h->ev_out = nullptr;
+    h->st = nullptr;
+    h->own_stream = false;
+  }
 }
 
 static jfft_status validate_material(jfft_solver* h, const jfft_material* m, int64_t N, bool field_on_device = false) {
@@ -387,6 +480,16 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   cudaError_t ce = cudaSetDevice(h->device);
   if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaSetDevice"));
   h->st = (cudaStream_t)o.stream;
+  if (!h->st) {
+    ce = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaStreamCreateWithFlags"));
+    h->own_stream = true;
+    ce = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaEventCreateWithFlags"));
+    cudaEventRecord(h->ev_in, cudaStreamLegacy);
+    cudaStreamWaitEvent(h->st, h->ev_in, 0);
+  }
   g_cur = h;
 
   // workspace plan
@@ -436,6 +539,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->red, 1024 * sizeof(double));
   AL(h->cg, nbmax * sizeof(CgState));
   AL(h->stage_cnt, nbmax * sizeof(unsigned));
+  AL(h->chunks_d, sizeof(int));
   ce = cudaMemset(h->stage_cnt, 0, nbmax * sizeof(unsigned));
   if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMemset"));
   AL(h->shifts, nbmax * sizeof(StrainShift));
@@ -459,6 +563,8 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   ce = cudaMallocHost((void**)&h->red_h, 1024 * sizeof(double));
   if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
   ce = cudaMallocHost((void**)&h->active_h, nbmax * sizeof(int));
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
+  ce = cudaMallocHost((void**)&h->chunks_h, sizeof(int));
   if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "cudaMallocHost"));
 
   for (int a = 0; a < d; ++a) {
@@ -567,6 +673,134 @@ static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, i
   return JFFT_OK;
 }
 
+// One check_every-iteration chunk of the PCG loop: q = K p (alpha), x and r update
+// (residual test), z = M^-1 r (beta), p = z + beta p. Right-hand sides that are
+// done skip every kernel, so a chunk may run past convergence at no cost.
+template <typename T>
+static cudaError_t pcg_chunk(jfft_solver* h, const Work<T>& w, int nb, int pc, double tol, int stop_mode, int chunk) {
+  const Grid& g = h->g;
+  const int64_t fe = field_elems(h);
+  auto stage = [&](int k) { return StageCtl{k, stop_mode, h->max_iter, tol, h->stage_cnt}; };
+  int np = 0;
+  cudaError_t e;
+  for (int c = 0; c < chunk; ++c) {
+    if ((e = apply_op(h, w, w.p, w.q, nb, 1, &np, h->cg, stage(kStageAlpha))) != cudaSuccess) return e;
+    if ((e = launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st, stage(kStageRR))) != cudaSuccess)
+      return e;
+    if ((e = precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageBeta))) != cudaSuccess) return e;
+    if ((e = launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Launches one chunk, replaying a captured CUDA graph of it when allowed. The graph
+// is captured on first use for a (nb, preconditioner, stopping rule, cap, chunk)
+// combination; kernel arguments and buffers are otherwise fixed per solver.
+template <typename T>
+static cudaError_t pcg_chunk_launch(jfft_solver* h, const Work<T>& w, int nb, int pc, double tol, int stop_mode,
+                                    int chunk) {
+  if (!h->opt.graphs || !h->graphs_ok) return pcg_chunk<T>(h, w, nb, pc, tol, stop_mode, chunk);
+  jfft_solver::ChunkGraph& gr = h->graph[sizeof(T) == 4 ? 1 : 0];
+  if (!gr.exec || gr.nb != nb || gr.pc != pc || gr.tol != tol || gr.stop_mode != stop_mode ||
+      gr.max_iter != h->max_iter || gr.chunk != chunk || gr.prof != h->profiling) {
+    drop_graph(h, gr);
+    cudaGraph_t graph = nullptr;
+    const int64_t l0 = h->launches;
+    const size_t p0 = h->pend.size();  // timing events recorded inside the capture belong to the graph
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      h->capturing = true;
+      const cudaError_t el = pcg_chunk<T>(h, w, nb, pc, tol, stop_mode, chunk);
+      h->capturing = false;
+      e = cudaStreamEndCapture(h->st, &graph);
+      if (e == cudaSuccess) e = el;
+    }
+    const int64_t captured = h->launches - l0;
+    h->launches = l0;
+    gr.events.assign(h->pend.begin() + p0, h->pend.end());
+    h->pend.resize(p0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gr.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      // capture is unavailable here: clear the error state and launch directly from now on
+      cudaGetLastError();
+      drop_graph(h, gr);
+      h->graphs_ok = false;
+      return pcg_chunk<T>(h, w, nb, pc, tol, stop_mode, chunk);
+    }
+    gr.nb = nb;
+    gr.pc = pc;
+    gr.tol = tol;
+    gr.stop_mode = stop_mode;
+    gr.max_iter = h->max_iter;
+    gr.chunk = chunk;
+    gr.launches = captured;
+    gr.prof = h->profiling;
+  }
+  h->launches += gr.launches;
+  h->graph_replays++;
+  if (gr.prof) h->replayed = &gr;  // the caller syncs before the next replay
+  return cudaGraphLaunch(gr.exec, h->st);
+}
+
+// Builds (or reuses) the CUDA graph of a whole PCG solve: a WHILE conditional node
+// whose body is one chunk followed by the condition kernel. Returns false if the
+// graph cannot be built here (the caller then polls from the host).
+template <typename T>
+static bool loop_graph_ready(jfft_solver* h, const Work<T>& w, int nb, int pc, double tol, int stop_mode, int chunk,
+                             int cap_chunks) {
+  jfft_solver::LoopGraph& lg = h->loop[sizeof(T) == 4 ? 1 : 0];
+  if (lg.exec && lg.nb == nb && lg.pc == pc && lg.tol == tol && lg.stop_mode == stop_mode &&
+      lg.max_iter == h->max_iter && lg.chunk == chunk)
+    return true;
+  if (lg.exec) cudaGraphExecDestroy(lg.exec);
+  lg.exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  cudaGraphConditionalHandle cond = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  const int64_t l0 = h->launches;
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      h->capturing = true;
+      cudaError_t el = pcg_chunk<T>(h, w, nb, pc, tol, stop_mode, chunk);
+      if (el == cudaSuccess) el = launch_cg_continue(h->cg, nb, h->chunks_d, cap_chunks, cond, h->st);
+      h->capturing = false;
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(h->st, &captured);
+      if (e == cudaSuccess) e = el;
+    }
+  }
+  const int64_t per_chunk = h->launches - l0;
+  h->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&lg.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (lg.exec) cudaGraphExecDestroy(lg.exec);
+    lg.exec = nullptr;
+    h->loop_ok = false;
+    return false;
+  }
+  lg.nb = nb;
+  lg.pc = pc;
+  lg.tol = tol;
+  lg.stop_mode = stop_mode;
+  lg.max_iter = h->max_iter;
+  lg.chunk = chunk;
+  lg.launches_per_chunk = per_chunk;
+  return true;
+}
+
 // Runs PCG in working precision T on w.r (holding the right-hand side) from x = 0
 // for nb right-hand sides. The INIT_FF stage must have run on w.r.
 template <typename T>
@@ -580,19 +814,31 @@ static jfft_status pcg_core_t(jfft_solver* h, const Work<T>& w, int nb, int pc, 
   CK(cudaMemsetAsync(w.p, 0, nb * fe * sizeof(T), h->st));
   CK(cudaMemsetAsync(h->stage_cnt, 0, nb * sizeof(unsigned), h->st));
   // Each scalar stage runs in the last block of the kernel that produces its partials.
-  auto stage = [&](int k) { return StageCtl{k, stop_mode, h->max_iter, tol, h->stage_cnt}; };
-  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageInitGamma)));
+  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, StageCtl{kStageInitGamma, stop_mode, h->max_iter, tol, h->stage_cnt}));
   CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
   const int chunk = h->opt.check_every;
   int64_t launched = 0;
   const int64_t cap = (int64_t)h->max_iter + chunk;
-  while (true) {
-    for (int c = 0; c < chunk; ++c) {
-      CK(apply_op(h, w, w.p, w.q, nb, 1, &np, h->cg, stage(kStageAlpha)));
-      CK(launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st, stage(kStageRR)));
-      CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageBeta)));
-      CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
-    }
+  const int cap_chunks = (int)std::min<int64_t>(cap / chunk + 2, 1 << 30);
+  // Device-side loop: one graph launch runs chunks until every right-hand side is
+  // done (or cap_chunks chunks have run); the host reads the states once.
+  const bool device_loop = h->opt.graphs && h->graphs_ok && h->loop_ok && !h->profiling &&
+                           loop_graph_ready<T>(h, w, nb, pc, tol, stop_mode, chunk, cap_chunks);
+  if (device_loop) {
+    const jfft_solver::LoopGraph& lg = h->loop[sizeof(T) == 4 ? 1 : 0];
+    CK(cudaMemsetAsync(h->chunks_d, 0, sizeof(int), h->st));
+    CK(cudaGraphLaunch(lg.exec, h->st));
+    CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->chunks_h, h->chunks_d, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    s = sync(h);
+    if (s) return s;
+    h->launches += (int64_t)h->chunks_h[0] * lg.launches_per_chunk;
+    h->graph_replays += h->chunks_h[0];
+    for (int b = 0; b < nb; ++b)
+      if (h->cg_h[b].done == kRunning) return fail(h, JFFT_ERR_CUDA, "PCG driver exceeded its iteration cap");
+  }
+  while (!device_loop) {
+    CK(pcg_chunk_launch<T>(h, w, nb, pc, tol, stop_mode, chunk));
     launched += chunk;
     CK(cudaMemcpyAsync(h->cg_h, h->cg, nb * sizeof(CgState), cudaMemcpyDeviceToHost, h->st));
     s = sync(h);
@@ -985,6 +1231,7 @@ extern "C" jfft_status jfft_postprocess(jfft_solver* h, int count, const double*
 
 // ------------------------------------------------------------- instrumentation
 extern "C" int64_t jfft_launch_count(const jfft_solver* h) { return h ? h->launches : 0; }
+extern "C" int64_t jfft_graph_replays(const jfft_solver* h) { return h ? h->graph_replays : 0; }
 
 extern "C" jfft_status jfft_set_profiling(jfft_solver* h, int on) {
   if (!h) return JFFT_ERR_ARG;

@@ -208,6 +208,11 @@ cudaError_t launch_add_f32(double* u, const float* d, int64_t n, cudaStream_t st
 cudaError_t launch_sub_norm(const Grid& g, const double* f, const double* q, double* r, int nb, double* partial,
                             int* nparts, cudaStream_t st);
 // S4 / S7: scalar stages, one block per rhs.
+// Condition kernel of the device-side PCG loop (graph WHILE node): chunks[0] += 1,
+// condition = (any cg[b].done == running) && chunks[0] < cap.
+cudaError_t launch_cg_continue(const CgState* cg, int nb, int* chunks, int cap, cudaGraphConditionalHandle cond,
+                               cudaStream_t st);
+
 enum ScalarStage { kStageInitFF = 0, kStageInitGamma = 1, kStageAlpha = 2, kStageRR = 3, kStageBeta = 4 };
 cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,
                               int stop_mode, int max_iter, cudaStream_t st);

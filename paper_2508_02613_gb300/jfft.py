@@ -39,7 +39,8 @@ class JfftMaterial(ctypes.Structure):
 class JfftOptions(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("stop_mode", c_int), ("stream", c_void_p),
                 ("hbm_budget", c_size_t), ("check_every", c_int), ("io_memory", c_int), ("max_loads", c_int),
-                ("void_value", c_double), ("device", c_int), ("inner_tol", c_double), ("max_refine", c_int)]
+                ("void_value", c_double), ("device", c_int), ("inner_tol", c_double), ("max_refine", c_int),
+                ("graphs", c_int)]
 
 
 class JfftResult(ctypes.Structure):
@@ -75,6 +76,7 @@ _SIGNATURES = {
     "jfft_solve_rhs": (c_int, [c_void_p, c_int, c_void_p, c_double, c_int, c_void_p, c_void_p]),
     "jfft_postprocess": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "jfft_launch_count": (c_int64, [c_void_p]),
+    "jfft_graph_replays": (c_int64, [c_void_p]),
     "jfft_set_profiling": (c_int, [c_void_p, c_int]),
     "jfft_profile_json": (c_char_p, [c_void_p]),
     "jfft_workspace_bytes": (c_size_t, [c_void_p]),
@@ -146,7 +148,7 @@ class Solver:
     def __init__(self, shape, field, nu, kind="young", e_min=0.0, e_max=1.0, exponent=1.0, C_ref=None,
                  max_iter=100000, stop_mode="rel", stream=None, check_every=8, io="host", max_loads=6,
                  void_value=1.0, device=0, hbm_budget=0, pinned=False, precision="fp64", inner_tol=1e-3,
-                 max_refine=30):
+                 max_refine=30, graphs=True):
         self.lib = load()
         self.pinned = pinned
         self.shape = tuple(int(s) for s in shape)
@@ -172,6 +174,7 @@ class Solver:
         opt.precision = PRECISION[precision]
         opt.inner_tol = inner_tol
         opt.max_refine = max_refine
+        opt.graphs = 1 if graphs else 0
         self.precision = precision
         self.max_loads = max(max_loads, self.d)
         h = c_void_p()
@@ -310,6 +313,10 @@ class Solver:
     @property
     def launch_count(self) -> int:
         return int(self.lib.jfft_launch_count(self.h))
+
+    @property
+    def graph_replays(self) -> int:
+        return int(self.lib.jfft_graph_replays(self.h))
 
     @property
     def workspace_bytes(self) -> int:

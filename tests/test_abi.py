@@ -30,7 +30,7 @@ def test_status_strings_and_defaults(lib):
     lib.jfft_default_options(ctypes.byref(opt))
     assert opt.max_iter == 100000 and opt.check_every == 8 and opt.max_loads == 6
     assert opt.void_value == 1.0 and opt.io_memory == 0 and opt.stop_mode == 0
-    assert opt.precision == 0 and opt.inner_tol == 1e-3 and opt.max_refine == 30
+    assert opt.precision == 0 and opt.inner_tol == 1e-3 and opt.max_refine == 30 and opt.graphs == 1
 
 
 def test_sources_target_sm103a_only():
@@ -41,3 +41,4 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.jfft_solve(None, 1, None, 1e-6, 0, None) == jfft.JFFT_ERR_ARG
     assert lib.jfft_apply_K(None, 1, None, None) == jfft.JFFT_ERR_ARG
     assert lib.jfft_launch_count(None) == 0
+    assert lib.jfft_graph_replays(None) == 0

@@ -272,6 +272,26 @@ def test_deterministic_and_counts_launches():
     assert prof["apply_K"][0] > 0 and prof["fft_lines"][1] > 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(precision):
+    """The PCG chunk replayed as a CUDA graph gives bit-identical results to the same
+    kernels launched one by one, on the solver's own stream and on a caller stream."""
+    torch = pytest.importorskip("torch")
+    shape = (64, 32)
+    rho, _ = _problem(shape, 13)
+    outs = []
+    for graphs, stream in ((False, None), (True, None), (True, "torch")):
+        st = torch.cuda.Stream() if stream else None
+        s = _solver(shape, rho, graphs=graphs, precision=precision,
+                    stream=st.cuda_stream if st is not None else None)
+        out = s.solve(mandel_unit_loads(2), 1e-8, "green_jacobi")
+        assert (s.graph_replays > 0) == graphs
+        outs.append(out)
+    for o in outs[1:]:
+        assert np.array_equal(o["iters"], outs[0]["iters"])
+        assert np.array_equal(o["u"], outs[0]["u"]) and np.array_equal(o["C_hom"], outs[0]["C_hom"])
+
+
 def test_device_io_matches_host_io():
     torch = pytest.importorskip("torch")
     shape = (32, 64)
