@@ -303,6 +303,7 @@ def main():
                     help="subset of the contrast sweep (profiling runs)")
     ap.add_argument("--preconds", default=",".join(PRECONDS), help="subset of the preconditioners (profiling runs)")
     ap.add_argument("--legs", default="fp64,mixed", help="precision legs to run (profiling runs)")
+    ap.add_argument("--no-cells", action="store_true", help="skip the small-cell batch leg")
     args = ap.parse_args()
     CONTRASTS = tuple(float(c) for c in args.contrasts.split(","))
     PRECONDS = tuple(args.preconds.split(","))
@@ -438,6 +439,59 @@ def main():
             return out
         return None
 
+    def cells_leg():
+        """The 32 x 32 workload (16 modes |k| <= 4, seeds 0-9, E = 1e-4 + (1 - 1e-4) rho^2,
+        nu 0.3, eps_xx, tolerance 1e-6) as a batch of 1520 cells (ten seeds x 152) in one
+        launch per preconditioner, beside the same solves through one handle per cell."""
+        from paper_2508_02613_gb300.jfft import Cells
+        from synthetic import smooth_density
+        shape, n_rep = (32, 32), 152
+        rho10 = np.stack([smooth_density(shape, 16, 4.0, sd) for sd in range(10)])
+        fields = np.concatenate([rho10] * n_rep)
+        eps1 = np.array([[1.0, 0.0, 0.0]])
+        cb = Cells(shape, max_cells=len(fields), max_loads=1, stream=stream.cuda_stream)
+        single = Solver(shape, rho10[0], NU, kind="density", e_min=1e-4, e_max=1.0, exponent=2.0,
+                        stream=stream.cuda_stream, max_loads=1)
+        out = {"workload": "32x32, 16 modes |k|<=4, seeds 0-9 x 152 copies, contrast 1e4, rho^2, nu 0.3, eps_xx, tol 1e-6",
+               "cells": len(fields), "dtype": "f64"}
+        # FP64 flops per cell and PCG iteration (model): operator ~120 per element, two
+        # packed complex 2D FFTs at 5 log2(N) per node each, symbol block 16, vectors 20
+        flops_it = 32 * 32 * (120 + 2 * 5 * 10 + 16 + 20)
+        for pc in ("green_jacobi", "green"):
+            kw = dict(kind="density", e_min=1e-4, e_max=1.0, exponent=2.0)
+            cb.solve(fields, NU, eps1, 1e-6, pc, **kw)
+            ts = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = cb.solve(fields, NU, eps1, 1e-6, pc, **kw)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.mean(ts)
+            its = res["iters"][:10, 0].tolist()
+            t_single = []
+            for sd in range(10):
+                single.set_material(rho10[sd], e_min=1e-4)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one = single.solve(eps1, 1e-6, pc, want_stress=False)
+                e1.record(stream)
+                e1.synchronize()
+                t_single.append(e0.elapsed_time(e1))
+            n_it = float(res["iters"].sum())
+            out[pc] = {"solves_per_s": len(fields) / (ms / 1e3), "batch_ms": ms,
+                       "us_per_solve": 1e3 * ms / len(fields), "iters_seeds_0_9": [int(v) for v in its],
+                       "single_handle_ms_per_solve": statistics.mean(t_single),
+                       "single_handle_iters": int(one["iters"][0]),
+                       "batch_speedup": statistics.mean(t_single) / (ms / len(fields)),
+                       "rel_res_max": float(res["rel_res"].max()),
+                       "fp64_tflops_model": n_it * flops_it / (ms / 1e3) / 1e12,
+                       "fp64_peak_tflops": FP64_PEAK_TFLOPS}
+        cb.close()
+        single.close()
+        return out
+
     legs = args.legs.split(",")
     fp64 = run_leg("fp64") if "fp64" in legs else None
     mixed = run_leg("mixed") if "mixed" in legs else None
@@ -481,6 +535,8 @@ def main():
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
         sh.close()
 
+    cells_line = cells_leg() if not args.no_cells else None
+
     mixed_line = None if mixed is None else {
         "value": mixed["value"], "unit": "solves/s", "ms_per_step": mixed["ms"], "speedup_vs_fp64": fp64["ms"] / mixed["ms"],
         "dtype": "f32 inner PCG (operator, FFT, preconditioner, vectors) + f64 scalars, residual and solution",
@@ -515,7 +571,7 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written before each timed step (outside the timed interval)"},
             "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": launches // args.steps,
-            "clocks": clk, "mixed": mixed_line,
+            "clocks": clk, "mixed": mixed_line, "small_cells": cells_line,
             "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
                        "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in fp64["rec"].items()},
                        "rel_res_max": max(max(v["rel_res"]) for v in fp64["rec"].values()),

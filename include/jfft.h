@@ -250,6 +250,44 @@ jfft_status jfft_postprocess(jfft_solver* h, int count, const double* eps_bar, c
 jfft_status jfft_apply_K_dot_noalloc(const jfft_grid* grid, double nu, const double* E, const double* x,
                                      double* y, double* xy, void* stream);
 
+/* ---- small-cell batches (many cells in one launch) ----
+ *
+ * Many independent periodic cells of one small 2D grid, each with its own material
+ * field, Poisson ratio and lower Young's modulus, all solved for the same
+ * macroscopic strains (paper Sec. 2 cell problem, Green or Green-Jacobi PCG of
+ * Sec. 3, Alg. 1 symbol with each cell's mean material as reference). One CUDA
+ * block per (cell, load case) runs the whole solve in shared memory, FP64, with
+ * the stopping rule, iteration cap and void value of the options.
+ */
+typedef struct jfft_cells jfft_cells;
+
+/* grid: dim 2, n[0], n[1] powers of two in [4, 32]; max_cells: largest batch;
+ * opt: as for jfft_create (precision must be FP64; max_loads bounds n_loads;
+ * io_memory applies to the field and result arrays of jfft_cells_solve).
+ * JFFT_ERR_UNSUPPORTED for other grids or precisions, JFFT_ERR_OOM if the
+ * workspace does not fit. The message of a failed call: jfft_cells_last_error(NULL). */
+jfft_status jfft_cells_create(jfft_cells** out, const jfft_grid* grid, int max_cells, const jfft_options* opt);
+
+/* mat->field: [n_cells][N] material fields (host or device memory per io_memory),
+ * mapped by mat->kind with mat->e_max and mat->exponent; nu_cells and e_min_cells:
+ * [n_cells] per-cell values in host memory, or NULL for mat->nu / mat->e_min.
+ * eps_bar: [n_loads][3] Mandel strains (host memory).
+ * Results (NULL entries skipped): res->u [n_cells][n_loads][2][N] zero-mean
+ * displacement; res->C_hom [n_cells][3][n_loads]; res->iters and res->rel_res
+ * [n_cells][n_loads] (true ||f - K u|| / ||f||). res->stress and
+ * res->refine_steps are not written.
+ * Returns JFFT_ERR_NOCONV / JFFT_ERR_BREAKDOWN if any (cell, load) did not
+ * converge / broke down (all results are still written), JFFT_ERR_ARG for bad
+ * arguments, JFFT_ERR_UNSUPPORTED for other preconditioners. */
+jfft_status jfft_cells_solve(jfft_cells* h, int n_cells, const jfft_material* mat, const double* nu_cells,
+                             const double* e_min_cells, int n_loads, const double* eps_bar, double tol,
+                             jfft_precond pc, jfft_result* res);
+
+void jfft_cells_destroy(jfft_cells* h);
+const char* jfft_cells_last_error(const jfft_cells* h);
+/* Kernel launches of this handle (one per jfft_cells_solve). */
+int64_t jfft_cells_launch_count(const jfft_cells* h);
+
 /* ---- instrumentation ---- */
 
 /* Number of kernels this handle has launched since creation (kernels inside a

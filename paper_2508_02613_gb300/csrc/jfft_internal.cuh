@@ -213,6 +213,16 @@ cudaError_t launch_sub_norm(const Grid& g, const double* f, const double* q, dou
 cudaError_t launch_cg_continue(const CgState* cg, int nb, int* chunks, int cap, cudaGraphConditionalHandle cond,
                                cudaStream_t st);
 
+// Small cells (2D, n0, n1 powers of two in [4, 32], FP64): one CTA per (cell, load)
+// runs the whole solve in shared memory. Arrays: field [n_cells][N], e_min, ec,
+// jscale [n_cells][2], shifts [n_loads]; outputs u [n_cells][n_loads][2][N] (may be
+// NULL), chom [n_cells][3][n_loads], iters / rel_res / status [n_cells][n_loads].
+size_t cells_smem_bytes(int N, int n0, int n1);
+cudaError_t launch_cells(int n0, int n1, int n_cells, int n_loads, int kind, double e_max, double exponent,
+                         const double* field, const double* e_min, const ElemConst* ec, const double* jscale,
+                         const StrainShift* shifts, double tol, int stop_mode, int max_iter, int pc, double void_js,
+                         double* u, double* chom, int* iters, double* rel_res, int* status, cudaStream_t st);
+
 enum ScalarStage { kStageInitFF = 0, kStageInitGamma = 1, kStageAlpha = 2, kStageRR = 3, kStageBeta = 4 };
 cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,
                               int stop_mode, int max_iter, cudaStream_t st);

@@ -75,6 +75,12 @@ _SIGNATURES = {
     "jfft_apply_precond": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "jfft_solve_rhs": (c_int, [c_void_p, c_int, c_void_p, c_double, c_int, c_void_p, c_void_p]),
     "jfft_postprocess": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "jfft_cells_create": (c_int, [POINTER(c_void_p), POINTER(JfftGrid), c_int, POINTER(JfftOptions)]),
+    "jfft_cells_solve": (c_int, [c_void_p, c_int, POINTER(JfftMaterial), c_void_p, c_void_p, c_int, c_void_p,
+                                 c_double, c_int, POINTER(JfftResult)]),
+    "jfft_cells_destroy": (None, [c_void_p]),
+    "jfft_cells_last_error": (ctypes.c_char_p, [c_void_p]),
+    "jfft_cells_launch_count": (c_int64, [c_void_p]),
     "jfft_launch_count": (c_int64, [c_void_p]),
     "jfft_graph_replays": (c_int64, [c_void_p]),
     "jfft_set_profiling": (c_int, [c_void_p, c_int]),
@@ -328,3 +334,78 @@ class Solver:
     def profile(self) -> dict:
         import json
         return json.loads(self.lib.jfft_profile_json(self.h).decode())
+
+
+class Cells:
+    """Batch of small 2D cells solved in one launch (jfft_cells_*): one grid shape
+    (n0, n1 powers of two in [4, 32]), per-cell material fields, Poisson ratios and
+    lower moduli, shared macroscopic strains."""
+
+    def __init__(self, shape, max_cells, max_loads=3, max_iter=100000, stop_mode="rel", stream=None,
+                 io="host", void_value=1.0, device=0):
+        self.lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        self.N = int(np.prod(self.shape))
+        self.io = io
+        g = JfftGrid(len(self.shape), (c_int64 * 3)(*(list(self.shape) + [0] * (3 - len(self.shape)))))
+        opt = JfftOptions()
+        self.lib.jfft_default_options(ctypes.byref(opt))
+        opt.max_iter = max_iter
+        opt.stop_mode = STOP[stop_mode]
+        opt.stream = c_void_p(stream) if stream else None
+        opt.io_memory = MEM[io]
+        opt.max_loads = max_loads
+        opt.void_value = void_value
+        opt.device = device
+        h = c_void_p()
+        st = self.lib.jfft_cells_create(ctypes.byref(h), ctypes.byref(g), int(max_cells), ctypes.byref(opt))
+        if st != JFFT_OK:
+            raise JfftError(st, self.lib.jfft_cells_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.jfft_cells_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, shape, dtype=np.float64):
+        if self.io == "host":
+            return np.empty(shape, dtype=dtype)
+        import torch
+        return torch.empty(shape, dtype=torch.float64 if dtype == np.float64 else torch.int32, device="cuda")
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.jfft_cells_launch_count(self.h))
+
+    def solve(self, fields, nu, eps_bar, tol, precond="green_jacobi", kind="young", e_min=0.0, e_max=1.0,
+              exponent=1.0, want_u=True):
+        """fields [n_cells, *shape]; nu and e_min scalars or [n_cells] arrays."""
+        n_cells = int(fields.shape[0])
+        nu_a = np.broadcast_to(np.asarray(nu, dtype=np.float64), (n_cells,)).copy()
+        em_a = np.broadcast_to(np.asarray(e_min, dtype=np.float64), (n_cells,)).copy()
+        eps = _f64(np.atleast_2d(eps_bar))
+        nl = int(eps.shape[0])
+        if self.io == "host":
+            self._fields = _f64(fields).reshape(n_cells, -1)
+            fptr = self._fields.ctypes.data_as(POINTER(c_double))
+        else:
+            self._fields = fields
+            fptr = ctypes.cast(c_void_p(fields.data_ptr()), POINTER(c_double))
+        mat = JfftMaterial(MATERIAL[kind], fptr, float(nu_a[0]), float(em_a[0]), e_max, exponent)
+        u = self._out((n_cells, nl, 2) + self.shape) if want_u else None
+        chom = self._out((n_cells, 3, nl))
+        its = self._out((n_cells, nl), np.int32)
+        rel = self._out((n_cells, nl))
+        res = JfftResult(_ptr(u), None, _ptr(chom), _ptr(its), _ptr(rel), None)
+        st = self.lib.jfft_cells_solve(self.h, n_cells, ctypes.byref(mat), _ptr(nu_a), _ptr(em_a), nl, _ptr(eps),
+                                       float(tol), PRECOND[precond], ctypes.byref(res))
+        if st not in (JFFT_OK, JFFT_ERR_NOCONV, JFFT_ERR_BREAKDOWN):
+            raise JfftError(st, self.lib.jfft_cells_last_error(self.h).decode())
+        return {"u": u, "C_hom": chom, "iters": its, "rel_res": rel, "status": st}

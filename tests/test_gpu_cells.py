@@ -1,0 +1,156 @@
+"""Small-cell batches (jfft_cells_*): one CUDA block per (cell, load) runs the whole
+solve. Parity against the FP64 oracle and the one-cell-per-handle GPU path, with the
+tolerances of the parity rule (converged solves: displacement 1e-10, homogenised
+stiffness 1e-9; runs stopped at tau: iteration counts within one of the oracle's
+range over two summation orders, displacement within 10 tau)."""
+
+import numpy as np
+import pytest
+
+from oracle import dense, fe, material, post, solve as osolve
+from synthetic import mandel_unit_loads, smooth_density
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _cells(shape, n_cells, seed0=0, modes=16, kmax=4.0):
+    rho = np.stack([smooth_density(shape, modes, kmax, seed0 + c) for c in range(n_cells)])
+    contrast = np.array([1e2, 1e3, 1e4, 3e4, 1e2, 1e4][:n_cells] * (n_cells // 6 + 1))[:n_cells]
+    nu = np.array([0.2, 0.3, 0.35, 0.4, 0.25, 0.3] * (n_cells // 6 + 1))[:n_cells]
+    return rho, 1.0 / contrast, nu
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+@pytest.mark.parametrize("pc", ["green_jacobi", "green"])
+@pytest.mark.parametrize("shape", [(32, 32), (16, 8), (4, 32)])
+def test_cells_converged_match_oracle(shape, pc):
+    from paper_2508_02613_gb300.jfft import Cells
+    n = 4
+    rho, e_min, nu = _cells(shape, n, seed0=3, kmax=3.0)
+    c = Cells(shape, max_cells=n, max_loads=3)
+    eps = mandel_unit_loads(2)
+    out = c.solve(rho, nu, eps, 1e-12, pc, kind="density", e_min=e_min, e_max=1.0, exponent=2.0)
+    assert out["status"] == 0
+    for k in range(n):
+        E = material.young_from_density(rho[k], e_min[k], 1.0, 2.0)
+        prob = osolve.setup(shape, E, nu[k])
+        ref = osolve.solve(prob, eps, 1e-12, pc)
+        nrm = np.linalg.norm(ref.u)
+        assert np.linalg.norm(out["u"][k] - ref.u) <= 1e-10 * nrm, k
+        assert rel(out["C_hom"][k], ref.C_hom) <= 1e-9, k
+        assert np.all(np.abs(out["iters"][k] - ref.iters) <= 1), (out["iters"][k], ref.iters)
+        assert out["rel_res"][k].max() <= 1e-11
+
+
+@pytest.mark.parametrize("pc", ["green_jacobi", "green"])
+def test_cells_32x32_workload(pc):
+    """The 32 x 32 workload (16 Fourier modes |k| <= 4, E = 1e-4 + (1 - 1e-4) rho^2,
+    nu 0.3, eps_xx = 1, tolerance 1e-6) for ten seeds in one launch."""
+    from paper_2508_02613_gb300.jfft import Cells
+    shape = (32, 32)
+    rho = np.stack([smooth_density(shape, 16, 4.0, s) for s in range(10)])
+    c = Cells(shape, max_cells=10, max_loads=1)
+    eps = mandel_unit_loads(2)[:1]
+    out = c.solve(rho, 0.3, eps, 1e-6, pc, kind="density", e_min=1e-4, e_max=1.0, exponent=2.0)
+    assert out["status"] == 0
+    assert c.launch_count == 1
+    for s in range(10):
+        E = material.young_from_density(rho[s], 1e-4, 1.0, 2.0)
+        prob = osolve.setup(shape, E, 0.3)
+        ref = osolve.solve(prob, eps, 1e-6, pc)
+        # iteration count: within one of the oracle, widened by the oracle's own spread
+        # between two summation orders (the residual can creep along the tolerance)
+        seq = osolve.solve(prob, eps, 1e-6, pc, dot_order="sequential")
+        lo = min(int(ref.iters[0]), int(seq.iters[0])) - 1
+        hi = max(int(ref.iters[0]), int(seq.iters[0])) + 1
+        assert lo <= int(out["iters"][s, 0]) <= hi, (s, out["iters"][s, 0], ref.iters[0], seq.iters[0])
+        assert np.linalg.norm(out["u"][s] - ref.u) <= 10 * 1e-6 * np.linalg.norm(ref.u)
+        assert out["rel_res"][s, 0] <= 2e-6
+
+
+def test_cells_equal_one_handle_per_cell():
+    """Each cell of the batch gives the result of its own one-cell Solver within the
+    stopping tolerance (the two paths round differently)."""
+    from paper_2508_02613_gb300.jfft import Cells, Solver
+    shape = (32, 16)
+    rho, e_min, nu = _cells(shape, 3, seed0=20)
+    eps = mandel_unit_loads(2)
+    c = Cells(shape, max_cells=3, max_loads=3)
+    out = c.solve(rho, nu, eps, 1e-8, "green_jacobi", kind="density", e_min=e_min, e_max=1.0, exponent=2.0)
+    for k in range(3):
+        s = Solver(shape, rho[k], nu[k], kind="density", e_min=e_min[k], e_max=1.0, exponent=2.0)
+        one = s.solve(eps, 1e-8, "green_jacobi")
+        assert np.all(np.abs(out["iters"][k] - one["iters"]) <= 1)
+        assert np.linalg.norm(out["u"][k] - one["u"]) <= 10 * 1e-8 * np.linalg.norm(one["u"])
+        assert rel(out["C_hom"][k], one["C_hom"]) <= 1e-7
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (8, 8)])
+def test_cells_match_dense_solve(shape):
+    from paper_2508_02613_gb300.jfft import Cells
+    rho, e_min, nu = _cells(shape, 2, seed0=40, modes=6, kmax=2.0)
+    c = Cells(shape, max_cells=2, max_loads=1)
+    eps = mandel_unit_loads(2)[-1:]
+    out = c.solve(rho, nu, eps, 1e-13, "green_jacobi", kind="density", e_min=e_min, e_max=1.0, exponent=2.0)
+    for k in range(2):
+        E = material.young_from_density(rho[k], e_min[k], 1.0, 2.0)
+        prob = osolve.setup(shape, E, nu[k])
+        from oracle import assemble
+        f = assemble.assemble_rhs(shape, E, prob.C, eps[0])
+        want = dense.dense_solve(prob.K, f)
+        assert np.linalg.norm(out["u"][k, 0] - want) <= 1e-10 * np.linalg.norm(want)
+        C_want = post.homogenised_stress(shape, E, prob.C, eps[0], want)
+        assert rel(out["C_hom"][k][:, 0], C_want) <= 1e-9
+
+
+def test_cells_homogeneous_cell_needs_no_iteration():
+    """Uniform material under a macroscopic strain: f = 0, zero iterations, u = 0 and
+    C_hom = E C_unit(nu) exactly as the Voigt = Reuss bound."""
+    from paper_2508_02613_gb300.jfft import Cells
+    shape = (16, 16)
+    fields = np.full((2,) + shape, 3.7)
+    c = Cells(shape, max_cells=2, max_loads=3)
+    out = c.solve(fields, np.array([0.3, 0.2]), mandel_unit_loads(2), 1e-10, "green")
+    assert np.all(out["iters"] == 0)
+    assert np.abs(out["u"]).max() == 0.0
+    for k, nu in enumerate((0.3, 0.2)):
+        assert rel(out["C_hom"][k], 3.7 * fe.C_unit(2, nu)) <= 1e-14
+
+
+def test_cells_device_io_matches_host_io():
+    torch = pytest.importorskip("torch")
+    from paper_2508_02613_gb300.jfft import Cells
+    shape = (16, 32)
+    rho, e_min, nu = _cells(shape, 3, seed0=60)
+    eps = mandel_unit_loads(2)
+    host = Cells(shape, max_cells=3).solve(rho, nu, eps, 1e-8, "green_jacobi", kind="density", e_min=e_min,
+                                            e_max=1.0, exponent=2.0)
+    dev = Cells(shape, max_cells=3, io="device").solve(torch.tensor(rho, device="cuda"), nu, eps, 1e-8,
+                                                       "green_jacobi", kind="density", e_min=e_min, e_max=1.0,
+                                                       exponent=2.0)
+    assert np.array_equal(host["u"], dev["u"].cpu().numpy())
+    assert np.array_equal(host["iters"], dev["iters"].cpu().numpy())
+
+
+def test_cells_argument_errors():
+    from paper_2508_02613_gb300.jfft import Cells, JfftError
+    with pytest.raises(JfftError):
+        Cells((64, 64), max_cells=1)
+    with pytest.raises(JfftError):
+        Cells((8, 8, 8), max_cells=1)
+    c = Cells((8, 8), max_cells=1)
+    with pytest.raises(JfftError):
+        c.solve(np.ones((1, 8, 8)), 0.7, mandel_unit_loads(2)[:1], 1e-8)
+    with pytest.raises(JfftError):
+        c.solve(-np.ones((1, 8, 8)), 0.3, mandel_unit_loads(2)[:1], 1e-8)
+    with pytest.raises(JfftError):
+        c.solve(np.ones((2, 8, 8)), 0.3, mandel_unit_loads(2)[:1], 1e-8)
