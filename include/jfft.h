@@ -176,6 +176,14 @@ const char* jfft_last_error(const jfft_solver* h);
 /* Per-handle settings. */
 jfft_status jfft_set_io_memory(jfft_solver* h, int io_memory);
 jfft_status jfft_set_max_iter(jfft_solver* h, int max_iter);
+/* Moves the handle to another stream (NULL: a stream the handle creates and owns),
+ * after finishing the work queued on the current one. Captured CUDA graphs stay valid. */
+jfft_status jfft_set_stream(jfft_solver* h, void* stream);
+
+/* Device workspace in bytes that jfft_create would allocate for this grid and these
+ * options (NULL options: defaults), without allocating. JFFT_ERR_ARG /
+ * JFFT_ERR_UNSUPPORTED for grids jfft_create would reject. */
+jfft_status jfft_workspace_estimate(const jfft_grid* grid, const jfft_options* opt, size_t* bytes);
 
 /* ---- building blocks of the path (same handle, same pointer rules) ---- */
 
@@ -287,6 +295,63 @@ void jfft_cells_destroy(jfft_cells* h);
 const char* jfft_cells_last_error(const jfft_cells* h);
 /* Kernel launches of this handle (one per jfft_cells_solve). */
 int64_t jfft_cells_launch_count(const jfft_cells* h);
+
+/* ---- request server with continuous batching ----
+ *
+ * Requests (grid, material field, load cases, tolerance, preconditioner and
+ * precision; each one a jfft_solve of the paper's cell problem) are queued on
+ * submission and run by max_active worker threads, each on its own CUDA stream, so
+ * the GPU overlaps the work of every running request. A queued request starts when
+ * a worker is free and its solver fits the device-memory budget: the workspace of
+ * every live solver (running or idle) counts; idle solvers of the same grid shape
+ * and precision are reused (material, Poisson ratio, Jacobi scaling and symbol are
+ * re-set); idle solvers of other shapes are evicted, least recently used first.
+ * Later requests that fit may start before an earlier one that does not. A result
+ * is the same as the request's solve alone (same kernel sequence, deterministic).
+ * The reference material is the mean material; max_loads is d(d+1)/2.
+ */
+typedef struct jfft_server jfft_server;
+
+typedef struct {
+  int max_active;            /* concurrent requests (worker threads / streams), 1..64 (default 4) */
+  size_t hbm_budget;         /* device bytes the solvers may hold; 0 = 80 % of the free memory at creation */
+  int device;                /* CUDA device ordinal (default 0) */
+} jfft_server_options;
+
+typedef struct {
+  jfft_grid grid;
+  jfft_material material;    /* field in host memory, copied at submission */
+  int n_loads;               /* 1..d(d+1)/2 */
+  const double* eps_bar;     /* [n_loads][d*] Mandel strains (host, copied) */
+  double tol;
+  int precond;               /* jfft_precond */
+  int precision;             /* jfft_precision */
+  int want_u;                /* 1: keep the displacement for jfft_server_wait */
+} jfft_request;
+
+typedef struct {
+  int64_t submitted, finished, queued, running;
+  size_t budget, used, peak_used;  /* bytes */
+  int64_t solvers_created, solvers_reused, solvers_evicted;
+} jfft_server_counters;
+
+void jfft_server_default_options(jfft_server_options* opt);
+jfft_status jfft_server_create(jfft_server** out, const jfft_server_options* opt);
+/* Queues a request (inputs copied); *id receives its id. JFFT_ERR_OOM if its
+ * solver can never fit the budget; JFFT_ERR_ARG / JFFT_ERR_UNSUPPORTED for bad
+ * requests. Does not wait for the GPU. */
+jfft_status jfft_server_submit(jfft_server* s, const jfft_request* req, int64_t* id);
+/* 0 queued, 1 running, 2 finished, -1 unknown id. */
+int jfft_server_poll(jfft_server* s, int64_t id);
+/* Waits for request id, copies its results into res (host arrays with the layout of
+ * jfft_solve; NULL entries skipped; u only if want_u), releases it and returns the
+ * solve's status. timing (may be NULL): [4] = seconds queued, seconds running,
+ * seconds from submission to completion, 1 if an idle solver was reused. */
+jfft_status jfft_server_wait(jfft_server* s, int64_t id, jfft_result* res, double* timing);
+jfft_status jfft_server_stats(jfft_server* s, jfft_server_counters* out);
+const char* jfft_server_last_error(jfft_server* s);
+/* Finishes the running requests, drops queued ones, frees every solver. */
+void jfft_server_destroy(jfft_server* s);
 
 /* ---- instrumentation ---- */
 

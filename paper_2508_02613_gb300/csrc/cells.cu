@@ -411,7 +411,7 @@ cudaError_t launch_cells(int n0, int n1, int n_cells, int n_loads, int kind, dou
   j.rel_res = rel_res;
   j.status = status;
   const size_t smem = cells_smem_bytes(j.N, n0, n1);
-  cudaError_t e = cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem(k_cells, smem);
   if (e != cudaSuccess) return e;
   JFFT_K("cells", st, k_cells<<<n_cells * n_loads, 256, smem, st>>>(j));
   return cudaGetLastError();

@@ -319,7 +319,7 @@ template <typename T> static size_t rows_smem(int L, int w, int ntw) {
 }
 
 template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = allow_dynamic_smem(kern, bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }

@@ -324,11 +324,97 @@ static jfft_status build_symbol(jfft_solver* h) {
   return JFFT_OK;
 }
 
+// Device workspace of a solver (bytes), as allocated by jfft_create.
+static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision) {
+  const int d = g.d;
+  const int64_t fe = (int64_t)d * g.N;
+  const int64_t spec_n = (int64_t)nbmax * d * g.F;
+  size_t total = 0;
+  total += 4 * g.N * sizeof(double);                               // field, E, esum, js
+  total += (size_t)g.F * ds * sizeof(double);                       // G
+  for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(double2);
+  total += (size_t)spec_n * sizeof(double2) * (d == 3 ? 2 : 1);     // T (U)
+  total += 5 * (size_t)nbmax * fe * sizeof(double);                 // x r p q z
+  total += (size_t)nbmax * 6 * kMaxPartials * sizeof(double);       // partial sums
+  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int) + sizeof(unsigned));
+  total += sizeof(int);                                             // chunk counter
+  if (precision == JFFT_PREC_MIXED) {
+    total += 2 * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
+    for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
+    total += (size_t)spec_n * sizeof(float2) * (d == 3 ? 2 : 1);
+    total += 5 * (size_t)nbmax * fe * sizeof(float);
+  }
+  return total;
+}
+
+// Grid of a jfft_grid, or an error message.
+static const char* make_grid(const jfft_grid* grid, Grid& g) {
+  if (!grid) return "grid is NULL";
+  const int d = grid->dim;
+  if (d != 2 && d != 3) return "dim must be 2 or 3";
+  const int nmax = d == 2 ? 2048 : 1024;
+  g = Grid{};
+  g.d = d;
+  g.N = 1;
+  for (int a = 0; a < d; ++a) {
+    const int64_t n = grid->n[a];
+    if (!is_pow2(n) || n < 4) return "each n must be a power of two >= 4";
+    if (n > nmax) return "grid exceeds the largest supported axis length";
+    g.n[a] = (int)n;
+    g.log2n[a] = ilog2i(n);
+    g.N *= n;
+  }
+  g.M = g.n[d - 1] / 2;
+  g.F = g.N / g.n[d - 1] * (g.M + 1);
+  return nullptr;
+}
+
+// Unit material C_unit(nu) of the operator, and the Jacobi constants derived from it:
+// kappa_a = diagonal entry of the unit element matrix for component a (the same at
+// every corner), jscale_a = kappa_a^-1/2.
+static void set_unit_material(jfft_solver* h, double nu) {
+  const Grid& g = h->g;
+  const int d = g.d;
+  h->nu = nu;
+  const double lam_u = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu_u = 1.0 / (2.0 * (1.0 + nu));
+  double hh[3];
+  for (int a = 0; a < d; ++a) hh[a] = 1.0 / g.n[a];
+  h->ec = make_elem_const(d, hh, lam_u, mu_u);
+  for (int a = 0; a < 3; ++a) h->kappa[a] = 1.0;
+  for (int a = 0; a < d; ++a) {
+    if (d == 2) {
+      double u[2][4] = {};
+      u[a][0] = 1.0;
+      element_force<2, double, false>(h->ec, nullptr, u, 1.0);
+      h->kappa[a] = u[a][0];
+    } else {
+      double u[3][8] = {};
+      u[a][0] = 1.0;
+      element_force<3, double, false>(h->ec, nullptr, u, 1.0);
+      h->kappa[a] = u[a][0];
+    }
+    h->jscale[a] = 1.0 / std::sqrt(h->kappa[a]);
+  }
+}
+
 static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool field_on_device) {
   const Grid& g = h->g;
   jfft_status s = validate_material(h, m, g.N, field_on_device);
   if (s) return s;
-  if (m->nu != h->nu) return fail(h, JFFT_ERR_ARG, "the Poisson ratio is fixed at creation");
+  if (m->nu != h->nu) {
+    if (!h->cref_mean) return fail(h, JFFT_ERR_ARG, "the Poisson ratio is fixed when C_ref was given explicitly");
+    s = sync(h);
+    if (s) return s;
+    set_unit_material(h, m->nu);
+    // captured graphs hold the element constants and Jacobi scales by value
+    for (auto& gr : h->graph) drop_graph(h, gr);
+    for (auto& lg : h->loop)
+      if (lg.exec) {
+        cudaGraphExecDestroy(lg.exec);
+        lg.exec = nullptr;
+      }
+  }
   CK(cudaMemcpyAsync(h->field, m->field, g.N * sizeof(double),
                      field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   if (field_on_device) {
@@ -393,23 +479,10 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   jfft_default_options(&o);
   if (opt) o = *opt;
   h->opt = o;
-  if (!grid) return bail(fail(h, JFFT_ERR_ARG, "grid is NULL"));
-  const int d = grid->dim;
-  if (d != 2 && d != 3) return bail(fail(h, JFFT_ERR_ARG, "dim must be 2 or 3"));
-  const int nmax = d == 2 ? 2048 : 1024;
   Grid& g = h->g;
-  g.d = d;
-  g.N = 1;
-  for (int a = 0; a < d; ++a) {
-    const int64_t n = grid->n[a];
-    if (!is_pow2(n) || n < 4) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "each n must be a power of two >= 4"));
-    if (n > nmax) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "grid exceeds the largest supported axis length"));
-    g.n[a] = (int)n;
-    g.log2n[a] = ilog2i(n);
-    g.N *= n;
-  }
-  g.M = g.n[d - 1] / 2;
-  g.F = g.N / g.n[d - 1] * (g.M + 1);
+  if (const char* ge = make_grid(grid, g))
+    return bail(fail(h, grid && (grid->dim == 2 || grid->dim == 3) ? JFFT_ERR_UNSUPPORTED : JFFT_ERR_ARG, ge));
+  const int d = g.d;
   h->ds = d * (d + 1) / 2;
   if (o.precision != JFFT_PREC_FP64 && o.precision != JFFT_PREC_MIXED)
     return bail(fail(h, JFFT_ERR_ARG, "unknown precision"));
@@ -437,11 +510,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   if (s) return bail(s);
 
   // unit material and reference material
-  const double lam_u = mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
-  const double mu_u = 1.0 / (2.0 * (1.0 + mat->nu));
-  double hh[3];
-  for (int a = 0; a < d; ++a) hh[a] = 1.0 / g.n[a];
-  h->ec = make_elem_const(d, hh, lam_u, mu_u);
+  set_unit_material(h, mat->nu);
   if (C_ref) {
     const int ds = h->ds;
     const double lam = C_ref[1], mu = 0.5 * (C_ref[0] - C_ref[1]);
@@ -457,22 +526,6 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
     h->cref_mean = false;
     h->cref_lam = lam;
     h->cref_mu = mu;
-  }
-  // kappa_a: diagonal of the unit element matrix (corner independent)
-  for (int a = 0; a < 3; ++a) h->kappa[a] = 1.0;
-  for (int a = 0; a < d; ++a) {
-    if (d == 2) {
-      double u[2][4] = {};
-      u[a][0] = 1.0;
-      element_force<2, double, false>(h->ec, nullptr, u, 1.0);
-      h->kappa[a] = u[a][0];
-    } else {
-      double u[3][8] = {};
-      u[a][0] = 1.0;
-      element_force<3, double, false>(h->ec, nullptr, u, 1.0);
-      h->kappa[a] = u[a][0];
-    }
-    h->jscale[a] = 1.0 / std::sqrt(h->kappa[a]);
   }
   h->void_js = 1.0 / std::sqrt(o.void_value);
   h->scale_store = 1.0 / (2.0 * (double)g.N);
@@ -496,21 +549,8 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   const int64_t fe = field_elems(h);
   const int nbmax = h->max_loads;
   const int64_t spec_n = (int64_t)nbmax * d * g.F;
-  size_t total = 0;
-  total += 4 * g.N * sizeof(double);                               // field, E, esum, js
-  total += (size_t)g.F * h->ds * sizeof(double);                    // G
-  for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(double2);
-  total += (size_t)spec_n * sizeof(double2) * (d == 3 ? 2 : 1);     // T (U)
-  total += 5 * (size_t)nbmax * fe * sizeof(double);                 // x r p q z
   const size_t part_rows = (size_t)nbmax * 6;
-  total += part_rows * kMaxPartials * sizeof(double);
-  total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int) + sizeof(unsigned));
-  if (o.precision == JFFT_PREC_MIXED) {
-    total += 2 * g.N * sizeof(float) + (size_t)g.F * h->ds * sizeof(float);
-    for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
-    total += (size_t)spec_n * sizeof(float2) * (d == 3 ? 2 : 1);
-    total += 5 * (size_t)nbmax * fe * sizeof(float);
-  }
+  const size_t total = plan_bytes(g, h->ds, nbmax, o.precision);
   if (o.hbm_budget && total > o.hbm_budget) {
     char msg[160];
     snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds hbm_budget %zu", total, o.hbm_budget);
@@ -1264,3 +1304,48 @@ extern "C" const char* jfft_profile_json(jfft_solver* h) {
 }
 
 extern "C" size_t jfft_workspace_bytes(const jfft_solver* h) { return h ? h->ws_bytes : 0; }
+
+extern "C" jfft_status jfft_workspace_estimate(const jfft_grid* grid, const jfft_options* opt, size_t* bytes) {
+  if (!bytes) return JFFT_ERR_ARG;
+  *bytes = 0;
+  Grid g;
+  if (make_grid(grid, g)) return grid && (grid->dim == 2 || grid->dim == 3) ? JFFT_ERR_UNSUPPORTED : JFFT_ERR_ARG;
+  jfft_options o;
+  jfft_default_options(&o);
+  if (opt) o = *opt;
+  int nbmax = o.max_loads <= 0 ? 6 : o.max_loads;
+  if (nbmax < g.d) nbmax = g.d;
+  if (nbmax > kMaxLoads) return JFFT_ERR_ARG;
+  if (o.precision != JFFT_PREC_FP64 && o.precision != JFFT_PREC_MIXED) return JFFT_ERR_ARG;
+  *bytes = plan_bytes(g, g.d * (g.d + 1) / 2, nbmax, o.precision);
+  return JFFT_OK;
+}
+
+extern "C" jfft_status jfft_set_stream(jfft_solver* h, void* stream) {
+  if (!h) return JFFT_ERR_ARG;
+  CurGuard guard(nullptr);
+  cudaSetDevice(h->device);
+  CK(cudaStreamSynchronize(h->st));
+  if (h->own_stream) {
+    if (stream) {
+      cudaStreamDestroy(h->st);
+      cudaEventDestroy(h->ev_in);
+      cudaEventDestroy(h->ev_out);
+      h->ev_in = h->ev_out = nullptr;
+      h->own_stream = false;
+      h->st = (cudaStream_t)stream;
+    }
+    return JFFT_OK;
+  }
+  if (stream) {
+    h->st = (cudaStream_t)stream;
+    return JFFT_OK;
+  }
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  h->st = st;
+  h->own_stream = true;
+  return JFFT_OK;
+}

@@ -90,6 +90,22 @@ struct CgState {
 
 enum CgDone { kRunning = 0, kConverged = 1, kNoConv = 2, kBreakdown = 3 };
 
+// Raises a kernel's dynamic shared-memory limit to the largest value the device allows
+// for it (opt-in maximum minus the kernel's static shared memory). Every caller sets the
+// same value, so launches from several host threads cannot lower the limit under one
+// another. cudaErrorInvalidValue if `bytes` exceeds that limit.
+template <typename K> inline cudaError_t allow_dynamic_smem(K* kern, size_t bytes) {
+  int dev = 0, mx = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa = {};
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  const size_t lim = (size_t)mx > fa.sharedSizeBytes ? (size_t)mx - fa.sharedSizeBytes : 0;
+  if (bytes > lim) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+}
+
 // Reduction buffers: partial sums per (row, block), reduced in a fixed order.
 constexpr int kMaxPartials = 1 << 17;
 

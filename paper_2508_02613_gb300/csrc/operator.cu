@@ -326,7 +326,7 @@ static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const T* E,
   MarchGeom m = march_geom<D>(g);
   const size_t smem = march_smem<D, T>(m);
   auto kern = k_apply_K<T, D, DOT, HAS_X, HAS_E, SHIFT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, nb);
   // one element per thread per layer; warps round up (owners are the first P1*P2)
@@ -383,7 +383,7 @@ static cudaError_t apply_K_dot_capped_t(const Grid& g, const ElemConst& ec, cons
   if (tiles * (g.n[0] / m.seg) > cap) return cudaErrorInvalidValue;
   const size_t smem = march_smem<D>(m);
   auto kern = k_apply_K<double, D, 1, true, true, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, 1);
   const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;

@@ -48,6 +48,21 @@ class JfftResult(ctypes.Structure):
                 ("rel_res", c_void_p), ("refine_steps", c_void_p)]
 
 
+class JfftServerOptions(ctypes.Structure):
+    _fields_ = [("max_active", c_int), ("hbm_budget", c_size_t), ("device", c_int)]
+
+
+class JfftRequest(ctypes.Structure):
+    _fields_ = [("grid", JfftGrid), ("material", JfftMaterial), ("n_loads", c_int), ("eps_bar", c_void_p),
+                ("tol", c_double), ("precond", c_int), ("precision", c_int), ("want_u", c_int)]
+
+
+class JfftServerCounters(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("finished", c_int64), ("queued", c_int64), ("running", c_int64),
+                ("budget", c_size_t), ("used", c_size_t), ("peak_used", c_size_t),
+                ("solvers_created", c_int64), ("solvers_reused", c_int64), ("solvers_evicted", c_int64)]
+
+
 class JfftError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"jfft status {status}: {msg}")
@@ -83,9 +98,19 @@ _SIGNATURES = {
     "jfft_cells_launch_count": (c_int64, [c_void_p]),
     "jfft_launch_count": (c_int64, [c_void_p]),
     "jfft_graph_replays": (c_int64, [c_void_p]),
+    "jfft_server_default_options": (None, [POINTER(JfftServerOptions)]),
+    "jfft_server_create": (c_int, [POINTER(c_void_p), POINTER(JfftServerOptions)]),
+    "jfft_server_submit": (c_int, [c_void_p, POINTER(JfftRequest), POINTER(c_int64)]),
+    "jfft_server_poll": (c_int, [c_void_p, c_int64]),
+    "jfft_server_wait": (c_int, [c_void_p, c_int64, POINTER(JfftResult), c_void_p]),
+    "jfft_server_stats": (c_int, [c_void_p, POINTER(JfftServerCounters)]),
+    "jfft_server_last_error": (ctypes.c_char_p, [c_void_p]),
+    "jfft_server_destroy": (None, [c_void_p]),
     "jfft_set_profiling": (c_int, [c_void_p, c_int]),
     "jfft_profile_json": (c_char_p, [c_void_p]),
     "jfft_workspace_bytes": (c_size_t, [c_void_p]),
+    "jfft_workspace_estimate": (c_int, [POINTER(JfftGrid), POINTER(JfftOptions), POINTER(c_size_t)]),
+    "jfft_set_stream": (c_int, [c_void_p, c_void_p]),
     "jfft_apply_K_dot_noalloc": (c_int, [POINTER(JfftGrid), c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_void_p]),
 }
@@ -225,10 +250,12 @@ class Solver:
         return a
 
     # -- calls
-    def set_material(self, field, e_min=None, e_max=None, exponent=None):
+    def set_material(self, field, e_min=None, e_max=None, exponent=None, nu=None):
         """New material field (host array, or a CUDA tensor in device io mode); the
-        density map parameters may change, the kind and nu may not."""
-        kind, nu, e_min0, e_max0, exponent0 = self._mat_args
+        density map parameters and nu (with the mean reference material) may change,
+        the kind may not."""
+        kind, nu0, e_min0, e_max0, exponent0 = self._mat_args
+        nu = nu0 if nu is None else nu
         e_min = e_min0 if e_min is None else e_min
         e_max = e_max0 if e_max is None else e_max
         exponent = exponent0 if exponent is None else exponent
@@ -248,6 +275,9 @@ class Solver:
 
     def set_max_iter(self, m):
         self._check(self.lib.jfft_set_max_iter(self.h, int(m)))
+
+    def set_stream(self, stream):
+        self._check(self.lib.jfft_set_stream(self.h, c_void_p(stream) if stream else None))
 
     def solve(self, eps_bar, tol, precond="green_jacobi", want_u=True, want_stress=True):
         eps = np.atleast_2d(_f64(eps_bar)) if self.io == "host" else eps_bar
@@ -409,3 +439,90 @@ class Cells:
         if st not in (JFFT_OK, JFFT_ERR_NOCONV, JFFT_ERR_BREAKDOWN):
             raise JfftError(st, self.lib.jfft_cells_last_error(self.h).decode())
         return {"u": u, "C_hom": chom, "iters": its, "rel_res": rel, "status": st}
+
+
+class Server:
+    """Request server with continuous batching (jfft_server_*): submit() queues a solve
+    and returns its id at once; wait(id) returns its results and timings."""
+
+    def __init__(self, max_active=4, hbm_budget=0, device=0):
+        self.lib = load()
+        opt = JfftServerOptions()
+        self.lib.jfft_server_default_options(ctypes.byref(opt))
+        opt.max_active = max_active
+        opt.hbm_budget = hbm_budget
+        opt.device = device
+        h = c_void_p()
+        st = self.lib.jfft_server_create(ctypes.byref(h), ctypes.byref(opt))
+        if st != JFFT_OK:
+            raise JfftError(st, "jfft_server_create failed")
+        self.h = h
+        self._meta = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.jfft_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, shape, field, nu, eps_bar, tol, precond="green_jacobi", precision="mixed", kind="young",
+               e_min=0.0, e_max=1.0, exponent=1.0, want_u=False) -> int:
+        shape = tuple(int(v) for v in shape)
+        d = len(shape)
+        fld = _f64(field).reshape(-1)
+        eps = _f64(np.atleast_2d(eps_bar))
+        g = JfftGrid(d, (c_int64 * 3)(*(list(shape) + [0] * (3 - d))))
+        mat = JfftMaterial(MATERIAL[kind], fld.ctypes.data_as(POINTER(c_double)), nu, e_min, e_max, exponent)
+        req = JfftRequest(g, mat, int(eps.shape[0]), eps.ctypes.data_as(c_void_p), float(tol), PRECOND[precond],
+                          PRECISION[precision], 1 if want_u else 0)
+        rid = c_int64()
+        st = self.lib.jfft_server_submit(self.h, ctypes.byref(req), ctypes.byref(rid))
+        if st != JFFT_OK:
+            raise JfftError(st, self.lib.jfft_server_last_error(self.h).decode())
+        self._meta[rid.value] = (shape, int(eps.shape[0]), bool(want_u))
+        return rid.value
+
+    def poll(self, rid) -> int:
+        return int(self.lib.jfft_server_poll(self.h, int(rid)))
+
+    def wait(self, rid):
+        shape, nl, want_u = self._meta.pop(rid)
+        d = len(shape)
+        ds = d * (d + 1) // 2
+        u = np.empty((nl, d) + shape) if want_u else None
+        chom = np.empty((ds, nl))
+        its = np.empty(nl, dtype=np.int32)
+        rel = np.empty(nl)
+        ref = np.empty(nl, dtype=np.int32)
+        res = JfftResult(_ptr(u), None, _ptr(chom), _ptr(its), _ptr(rel), _ptr(ref))
+        timing = np.zeros(4)
+        st = self.lib.jfft_server_wait(self.h, int(rid), ctypes.byref(res), _ptr(timing))
+        return {"u": u, "C_hom": chom, "iters": its, "rel_res": rel, "refine_steps": ref, "status": st,
+                "queued_s": float(timing[0]), "run_s": float(timing[1]), "latency_s": float(timing[2]),
+                "reused_solver": bool(timing[3])}
+
+    def stats(self) -> dict:
+        c = JfftServerCounters()
+        self.lib.jfft_server_stats(self.h, ctypes.byref(c))
+        return {f: int(getattr(c, f)) for f, _ in JfftServerCounters._fields_}
+
+
+def workspace_estimate(shape, precision="fp64", max_loads=6) -> int:
+    """Device bytes jfft_create would allocate for this grid (jfft_workspace_estimate)."""
+    lib = load()
+    shape = tuple(int(v) for v in shape)
+    g = JfftGrid(len(shape), (c_int64 * 3)(*(list(shape) + [0] * (3 - len(shape)))))
+    opt = JfftOptions()
+    lib.jfft_default_options(ctypes.byref(opt))
+    opt.precision = PRECISION[precision]
+    opt.max_loads = max_loads
+    out = c_size_t()
+    st = lib.jfft_workspace_estimate(ctypes.byref(g), ctypes.byref(opt), ctypes.byref(out))
+    if st != JFFT_OK:
+        raise JfftError(st, "unsupported grid")
+    return int(out.value)

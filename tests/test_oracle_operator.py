@@ -144,6 +144,20 @@ def test_preconditioners_are_symmetric(pc):
     assert abs(np.vdot(a, Mb) - np.vdot(b, Ma)) <= 1e-15 * np.linalg.norm(a) * np.linalg.norm(Mb) * 16
 
 
+@pytest.mark.parametrize("shape", [(8, 8), (32, 32), (4, 4, 4), (8, 8, 8)])
+def test_closed_form_symbol_equals_alg1(shape):
+    """The oracle's plane-wave closed form (used to bracket iteration counts) equals
+    Alg. 1 and the hand-derived formula of this file."""
+    d = len(shape)
+    C = 0.8 * fe.C_unit(d, 0.3)
+    K1, G1 = green.green_symbol(shape, C)
+    K2, G2 = green.closed_form_symbol(shape, C)
+    assert np.abs(K1 - K2).max() <= 1e-13 * np.abs(K1).max()
+    assert np.abs(G1 - G2).max() <= 1e-12 * np.abs(G1).max()
+    lam, mu = float(C[0, 1]), 0.5 * float(C[0, 0] - C[0, 1])
+    assert np.abs(K2 - _closed_form_symbol(shape, lam, mu)).max() <= 1e-13 * np.abs(K2).max()
+
+
 def test_library_fft_equals_explicit_dft():
     """numpy.fft (used as a library step) agrees with the explicit O(N^2) DFT, both in the
     symbol and in the application of the Green operator."""
