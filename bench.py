@@ -48,6 +48,7 @@ METRIC = "PCG solves/s"
 WORKLOAD = ("2D plane-strain periodic cell, 1024x1024 Q1 quads (4 Gauss points), FP64; smooth density "
             "(16 Fourier modes, |k|<=8), E = 1/c + (1-1/c) rho^2, c in {1e2,1e4,1e6}, nu 0.3, C_ref mean; "
             "3 Mandel unit loads; Green-Jacobi and Green PCG to 1e-8 relative residual")
+PROFILED_STEPS = 1   # steps of the per-kernel profiling pass after the timed steps
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # SMs x max clock x FP64 flop/clk/SM (2 DFMA)
 ITER_COUNTS = os.path.join(ROOT, "oracle", "data", "iters_2d_1024.json")
 
@@ -230,6 +231,8 @@ def oracle_iteration_counts():
         rows = json.load(fh)["solves"]
     out = {}
     for r in rows:
+        if r.get("symbol", "alg1") != "alg1":
+            continue
         out.setdefault((r["contrast"], r["precond"]), [0, 0, 0])[r["load"]] = r["iters"]
     return out
 
@@ -304,6 +307,9 @@ def main():
     ap.add_argument("--preconds", default=",".join(PRECONDS), help="subset of the preconditioners (profiling runs)")
     ap.add_argument("--legs", default="fp64,mixed", help="precision legs to run (profiling runs)")
     ap.add_argument("--no-cells", action="store_true", help="skip the small-cell batch leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-requests", type=int, default=40,
+                    help="requests of the seeded serving stream to replay (the full stream has 2000)")
     args = ap.parse_args()
     CONTRASTS = tuple(float(c) for c in args.contrasts.split(","))
     PRECONDS = tuple(args.preconds.split(","))
@@ -390,12 +396,12 @@ def main():
         launches = s.launch_count - n0
         replays = s.graph_replays - r0
         clk = clocks.stop()
-        # Per-kernel durations: the same steps again with a CUDA event pair around every
-        # kernel launch (the PCG chunk then runs as a replayed graph with event nodes
-        # instead of the device-side loop, which cannot hold event nodes).
+        # Per-kernel durations: one more step with a CUDA event pair around every kernel
+        # launch (the PCG chunk then runs as a replayed graph with event nodes instead of
+        # the device-side loop, which cannot hold event nodes).
         s.set_profiling(True)
         prof_times = []
-        for _ in range(args.steps):
+        for _ in range(PROFILED_STEPS):
             flush.fill_(1.0)
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,7 +422,7 @@ def main():
         """Dominant kernel with its achieved rate, from the per-kernel CUDA events of the
         profiling pass that repeats the timed steps. Units are right-hand-side applications:
         per load, one operator and one preconditioner per PCG iteration."""
-        n_units = sum(sum(r["iters"]) for r in leg["rec"].values()) * args.steps
+        n_units = sum(sum(r["iters"]) for r in leg["rec"].values()) * PROFILED_STEPS
         rows = sorted(((k, v[0], v[1]) for k, v in leg["prof"].items()), key=lambda r: -r[2])
         total_ms = sum(r[2] for r in rows)
         peak_gbs, peak_kind = hbm_peak_gbs()
@@ -492,6 +498,69 @@ def main():
         single.close()
         return out
 
+    def serving_leg():
+        """The serving stream: seeded requests with Poisson arrivals at 50/s, grids drawn from
+        2D {256^2 .. 2048^2} and 3D {64^3, 128^3, 256^3}, contrast log-uniform in [1e2, 1e6],
+        nu uniform in [0.2, 0.4], 1..d(d+1)/2 load cases, Green-Jacobi to 1e-8, mixed precision,
+        replayed in real time into the request server (4 workers). One smooth field per grid
+        (16 modes in 2D, 32 in 3D, |k| <= 8, seed 0; rho^2 in 2D, rho^3 in 3D) serves every
+        request of that grid; contrast and nu vary per request. The first 8 requests are also
+        solved one after another in plain FP64 (a new handle each, as a serial service would)."""
+        from paper_2508_02613_gb300.jfft import Server
+        from synthetic import smooth_density
+        rng = np.random.default_rng(0)
+        grids = [(256, 256), (512, 512), (1024, 1024), (2048, 2048), (64, 64, 64), (128, 128, 128),
+                 (256, 256, 256)]
+        n = args.serving_requests
+        reqs, t_arr = [], 0.0
+        for _ in range(n):
+            t_arr += rng.exponential(1.0 / 50.0)
+            gsh = grids[int(rng.integers(len(grids)))]
+            d = len(gsh)
+            ds = d * (d + 1) // 2
+            reqs.append((t_arr, gsh, float(10.0 ** rng.uniform(2, 6)), float(rng.uniform(0.2, 0.4)),
+                         int(rng.integers(1, ds + 1))))
+        fields = {gsh: smooth_density(gsh, 16 if len(gsh) == 2 else 32, 8.0, 0) for gsh in grids}
+        srv = Server(max_active=4)
+        t0 = time.perf_counter()
+        ids = []
+        for (ta, gsh, c, nu, nl) in reqs:
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.0005)
+            d = len(gsh)
+            ids.append(srv.submit(gsh, fields[gsh], nu, np.eye(d * (d + 1) // 2)[:nl], TOL, "green_jacobi", "mixed",
+                                  kind="density", e_min=1.0 / c, e_max=1.0, exponent=2.0 if d == 2 else 3.0))
+        outs = [srv.wait(i) for i in ids]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = sorted(o["latency_s"] for o in outs)
+        pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+        # serial plain FP64 on the first 8 requests
+        t_ser = 0.0
+        n_ser = min(8, n)
+        for (ta, gsh, c, nu, nl) in reqs[:n_ser]:
+            d = len(gsh)
+            t1 = time.perf_counter()
+            s1 = Solver(gsh, fields[gsh], nu, kind="density", e_min=1.0 / c, e_max=1.0,
+                        exponent=2.0 if d == 2 else 3.0, max_loads=d * (d + 1) // 2)
+            s1.solve(np.eye(d * (d + 1) // 2)[:nl], TOL, "green_jacobi", want_u=False, want_stress=False)
+            s1.close()
+            t_ser += time.perf_counter() - t1
+        served_first = sum(o["run_s"] for o in outs[:n_ser])
+        return {"workload": ("seeded stream, Poisson 50/s, 2D {256^2..2048^2} + 3D {64^3,128^3,256^3}, contrast "
+                             "log-U[1e2,1e6], nu U[0.2,0.4], 1..d* loads, Green-Jacobi to 1e-8, mixed precision"),
+                "requests": n, "of_stream": 2000, "offered_per_s": 50.0, "max_active": 4,
+                "wall_s": wall, "solves_per_s": n / wall,
+                "p50_latency_s": pct(0.50), "p99_latency_s": pct(0.99),
+                "mean_queue_s": statistics.mean(o["queued_s"] for o in outs),
+                "max_rel_res": max(float(o["rel_res"].max()) for o in outs),
+                "all_converged": all(o["status"] == 0 for o in outs),
+                "solvers": {k: st[k] for k in ("solvers_created", "solvers_reused", "solvers_evicted", "peak_used")},
+                "serial_fp64_first8_solves_per_s": n_ser / t_ser,
+                "served_mixed_first8_run_s_sum": served_first,
+                "note": "offered load exceeds capacity, so latency percentiles are queue-dominated"}
+
     legs = args.legs.split(",")
     fp64 = run_leg("fp64") if "fp64" in legs else None
     mixed = run_leg("mixed") if "mixed" in legs else None
@@ -536,6 +605,7 @@ def main():
         sh.close()
 
     cells_line = cells_leg() if not args.no_cells else None
+    serving_line = serving_leg() if not args.no_serving else None
 
     mixed_line = None if mixed is None else {
         "value": mixed["value"], "unit": "solves/s", "ms_per_step": mixed["ms"], "speedup_vs_fp64": fp64["ms"] / mixed["ms"],
@@ -571,7 +641,7 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written before each timed step (outside the timed interval)"},
             "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": launches // args.steps,
-            "clocks": clk, "mixed": mixed_line, "small_cells": cells_line,
+            "clocks": clk, "mixed": mixed_line, "small_cells": cells_line, "serving": serving_line,
             "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
                        "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in fp64["rec"].items()},
                        "rel_res_max": max(max(v["rel_res"]) for v in fp64["rec"].values()),
