@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--legs", default="fp64,mixed", help="precision legs to run (profiling runs)")
     ap.add_argument("--no-cells", action="store_true", help="skip the small-cell batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel from the host (profilers cannot see kernels inside conditional graphs)")
     ap.add_argument("--serving-requests", type=int, default=40,
                     help="requests of the seeded serving stream to replay (the full stream has 2000)")
     args = ap.parse_args()
@@ -355,7 +357,8 @@ def main():
         """Warm-up, one recording pass (iterations, time to tolerance per solve call),
         then the timed steps with per-kernel CUDA events and clock sampling."""
         s = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
-                   stream=stream.cuda_stream, io="device", max_loads=N_LOADS, precision=precision)
+                   stream=stream.cuda_stream, io="device", max_loads=N_LOADS, precision=precision,
+                   graphs=not args.no_graphs)
 
         def step(record=None):
             for c in CONTRASTS:

@@ -148,11 +148,19 @@ void jfft_default_options(jfft_options* opt);
 jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, const jfft_material* mat,
                         const double* C_ref, const jfft_options* opt);
 
-/* Replace the material field (same grid, nu and C_ref choice); recomputes E,
- * J^1/2 and, when C_ref was NULL, G_hat for the new mean (Alg. 1). No
- * reallocation. The field pointer follows the handle's io memory; a device field
- * is validated on the device (JFFT_ERR_ARG if any entry is negative or not finite). */
+/* Replace the material field (same grid and C_ref choice; nu may change when C_ref
+ * was NULL); recomputes E, J^1/2 and, when C_ref was NULL, G_hat for the new mean
+ * (Alg. 1). No reallocation. The field pointer follows the handle's io memory; a
+ * device field is validated on the device (JFFT_ERR_ARG if any entry is negative or
+ * not finite). */
 jfft_status jfft_set_material(jfft_solver* h, const jfft_material* mat);
+
+/* The same for a geometry G_p of pixels[a] (powers of two, <= n[a]) pixels per axis
+ * discretised on this grid T_n (Sec. 4 "Material data sampling", "Discretization and
+ * grid refinement": n >= p, pixel-wise constant data). mat->field holds one value
+ * per pixel, [p0][p1]([p2]) C order; every voxel takes the value of the pixel that
+ * contains it. JFFT_ERR_ARG for other pixel counts. */
+jfft_status jfft_set_material_coarse(jfft_solver* h, const jfft_material* mat, const int64_t* pixels);
 
 /*
  * Solve for n_loads macroscopic strains eps_bar [n_loads][d*] (Mandel): for each,

@@ -101,3 +101,47 @@ def apply_green(G_hat: np.ndarray, r: np.ndarray, explicit_dft: bool = False) ->
 def apply_green_jacobi(G_hat: np.ndarray, J_half: np.ndarray, r: np.ndarray) -> np.ndarray:
     """z = J^(1/2) F^-1 G_hat F J^(1/2) r (paper Eq. prec_lin_systemJG_2)."""
     return J_half * apply_green(G_hat, J_half * r)
+
+
+def closed_form_symbol(n, C_ref: np.ndarray):
+    """(K_hat, G_hat) of the uniform Q1 operator for an isotropic C_ref from the plane-wave
+    closed form (full Gauss rule), real [d, d, *n]. With t_a = 2 pi k_a / n_a,
+    one-minus-cosine written as 2 sin^2(t_a / 2):
+      2D: S_a = 2/3 (1 - cos t_a)(2 + cos t_b), K_12 = (lam + mu) sin t_1 sin t_2;
+      3D: S_a = 2h/9 (1 - cos t_a) prod_{b != a} (2 + cos t_b),
+          K_ab = (lam + mu) h/3 sin t_a sin t_b (2 + cos t_o) (o the third axis);
+      K_aa = (lam + 2 mu) S_a + mu sum_{b != a} S_b.
+    It equals Alg. 1 (green_symbol) up to rounding but has no cancellation at low
+    frequencies, where Alg. 1's transform of O(1) impulse-response entries carries a
+    relative error ~eps (n / 2 pi)^2. Used to bracket PCG iteration counts that react
+    to that rounding; the solver path itself follows Alg. 1. Square / cubic grids only
+    (the formula above is for h equal on every axis)."""
+    n = tuple(int(k) for k in n)
+    d = len(n)
+    if len(set(n)) != 1:
+        raise ValueError("closed_form_symbol needs equal axis lengths")
+    lam = float(C_ref[0, 1])
+    mu = 0.5 * float(C_ref[0, 0] - C_ref[0, 1])
+    th = np.meshgrid(*[2 * np.pi * np.arange(k) / k for k in n], indexing="ij")
+    c = [np.cos(t) for t in th]
+    s = [np.sin(t) for t in th]
+    omc = [2.0 * np.sin(0.5 * t) ** 2 for t in th]
+    h = 1.0 / n[0]
+    K = np.zeros((d, d) + n)
+    if d == 2:
+        S = [2.0 / 3.0 * omc[0] * (2.0 + c[1]), 2.0 / 3.0 * omc[1] * (2.0 + c[0])]
+        K[0, 1] = K[1, 0] = (lam + mu) * s[0] * s[1]
+    else:
+        S = [2.0 * h / 9.0 * omc[a] * np.prod([2.0 + c[b] for b in range(3) if b != a], axis=0) for a in range(3)]
+        for a in range(3):
+            for b in range(3):
+                if a != b:
+                    o = 3 - a - b
+                    K[a, b] = (lam + mu) * h / 3.0 * s[a] * s[b] * (2.0 + c[o])
+    for a in range(d):
+        K[a, a] = (lam + 2.0 * mu) * S[a] + mu * sum(S[b] for b in range(d) if b != a)
+    blocks = np.moveaxis(K.reshape(d, d, -1), 2, 0)
+    G_blocks = np.zeros_like(blocks)
+    G_blocks[1:] = np.linalg.inv(blocks[1:])
+    G_hat = np.moveaxis(G_blocks, 0, 2).reshape((d, d) + n)
+    return K, G_hat

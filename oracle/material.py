@@ -15,3 +15,17 @@ import numpy as np
 def young_from_density(rho: np.ndarray, e_min: float, e_max: float, exponent: float) -> np.ndarray:
     rho = np.asarray(rho, dtype=np.float64)
     return e_min + (e_max - e_min) * np.power(rho, exponent)
+
+
+def upsample(coarse: np.ndarray, n) -> np.ndarray:
+    """Geometry G_p on the grid T_n (Sec. 4 "Discretization and grid refinement", n >= p):
+    pixel-wise constant data, so every voxel takes the value of the pixel containing it;
+    each pixel covers (n_a / p_a) voxels along axis a."""
+    coarse = np.asarray(coarse, dtype=np.float64)
+    out = coarse
+    for a, na in enumerate(n):
+        pa = coarse.shape[a]
+        if na % pa:
+            raise ValueError("n must be a multiple of p on every axis")
+        out = np.repeat(out, na // pa, axis=a)
+    return out

@@ -398,9 +398,22 @@ static void set_unit_material(jfft_solver* h, double nu) {
   }
 }
 
-static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool field_on_device) {
+// coarse: pixels per axis of a geometry G_p (NULL: the field has one value per voxel).
+static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool field_on_device,
+                                  const int64_t* coarse = nullptr) {
   const Grid& g = h->g;
-  jfft_status s = validate_material(h, m, g.N, field_on_device);
+  int shift[3] = {0, 0, 0};
+  int64_t count = g.N;
+  if (coarse) {
+    count = 1;
+    for (int a = 0; a < g.d; ++a) {
+      const int64_t p = coarse[a];
+      if (!is_pow2(p) || p > g.n[a]) return fail(h, JFFT_ERR_ARG, "pixels per axis must be powers of two <= n");
+      shift[a] = g.log2n[a] - ilog2i(p);
+      count *= p;
+    }
+  }
+  jfft_status s = validate_material(h, m, count, field_on_device);
   if (s) return s;
   if (m->nu != h->nu) {
     if (!h->cref_mean) return fail(h, JFFT_ERR_ARG, "the Poisson ratio is fixed when C_ref was given explicitly");
@@ -415,8 +428,11 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
         lg.exec = nullptr;
       }
   }
-  CK(cudaMemcpyAsync(h->field, m->field, g.N * sizeof(double),
+  // a coarse geometry is staged in the E buffer and expanded into the voxel field
+  double* dst = coarse ? h->E : h->field;
+  CK(cudaMemcpyAsync(dst, m->field, count * sizeof(double),
                      field_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  if (coarse) CK(launch_upsample(g, shift, h->E, h->field, h->st));
   if (field_on_device) {
     int* bad = reinterpret_cast<int*>(h->red);
     CK(cudaMemsetAsync(bad, 0, sizeof(int), h->st));
@@ -628,6 +644,12 @@ extern "C" jfft_status jfft_set_material(jfft_solver* h, const jfft_material* m)
   if (!h) return JFFT_ERR_ARG;
   CurGuard guard(h);
   return setup_material(h, m, h->io == JFFT_MEM_DEVICE);
+}
+
+extern "C" jfft_status jfft_set_material_coarse(jfft_solver* h, const jfft_material* m, const int64_t* pixels) {
+  if (!h || !pixels) return JFFT_ERR_ARG;
+  CurGuard guard(h);
+  return setup_material(h, m, h->io == JFFT_MEM_DEVICE, pixels);
 }
 
 extern "C" const char* jfft_status_string(jfft_status s) {

@@ -133,6 +133,8 @@ void hook_end(const char* name, cudaStream_t st);
 // the number of partial sums written per row.
 
 // S1: E[i] = e_min + (e_max - e_min) field[i]^expo (kind 1) or E = field (kind 0).
+// fine[I] = coarse[pixel of I], pixel index i_a >> shift[a] (geometry G_p on T_n).
+cudaError_t launch_upsample(const Grid& g, const int* shift, const double* coarse, double* fine, cudaStream_t st);
 cudaError_t launch_material(const double* field, double* E, int64_t N, int kind, double e_min, double e_max,
                             double expo, cudaStream_t st);
 

@@ -33,6 +33,31 @@ cudaError_t launch_check_field(const double* f, int64_t N, int* bad, cudaStream_
   return cudaGetLastError();
 }
 
+// Geometry G_p on the grid T_n (Sec. 4 "Discretization and grid refinement", n >= p):
+// fine voxel I takes the value of the coarse pixel that contains it, index i_a >> s_a
+// with s_a = log2(n_a / p_a) per axis.
+__global__ void k_upsample(Grid g, int s0, int s1, int s2, const double* __restrict__ coarse, double* __restrict__ fine) {
+  const int p1 = g.n[1] >> s1, p2 = g.d == 3 ? (g.n[2] >> s2) : 1;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < g.N; I += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = I;
+    int i2 = 0;
+    if (g.d == 3) {
+      i2 = (int)(r % g.n[2]);
+      r /= g.n[2];
+    }
+    const int i1 = (int)(r % g.n[1]);
+    const int i0 = (int)(r / g.n[1]);
+    const int64_t c = ((int64_t)(i0 >> s0) * p1 + (i1 >> s1)) * p2 + (g.d == 3 ? (i2 >> s2) : 0);
+    fine[I] = coarse[c];
+  }
+}
+
+cudaError_t launch_upsample(const Grid& g, const int* shift, const double* coarse, double* fine, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((g.N + 255) / 256, 152 * 16);
+  JFFT_K("upsample", st, k_upsample<<<blocks, 256, 0, st>>>(g, shift[0], shift[1], shift[2], coarse, fine));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_material(const double* field, double* E, int64_t N, int kind, double e_min, double e_max,
                             double expo, cudaStream_t st) {
   int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "jfft_create": (c_int, [POINTER(c_void_p), POINTER(JfftGrid), POINTER(JfftMaterial), c_void_p,
                             POINTER(JfftOptions)]),
     "jfft_set_material": (c_int, [c_void_p, POINTER(JfftMaterial)]),
+    "jfft_set_material_coarse": (c_int, [c_void_p, POINTER(JfftMaterial), POINTER(c_int64)]),
     "jfft_solve": (c_int, [c_void_p, c_int, c_void_p, c_double, c_int, POINTER(JfftResult)]),
     "jfft_destroy": (None, [c_void_p]),
     "jfft_status_string": (c_char_p, [c_int]),
@@ -268,6 +269,25 @@ class Solver:
             fptr = ctypes.cast(c_void_p(field.data_ptr()), POINTER(c_double))
         mat = JfftMaterial(MATERIAL[kind], fptr, nu, e_min, e_max, exponent)
         self._check(self.lib.jfft_set_material(self.h, ctypes.byref(mat)))
+
+    def set_material_coarse(self, field, e_min=None, e_max=None, exponent=None, nu=None):
+        """Geometry G_p: field has p_a pixels per axis (powers of two, p_a <= n_a); every
+        voxel takes the value of its pixel (host array, or a CUDA tensor in device io)."""
+        kind, nu0, e_min0, e_max0, exponent0 = self._mat_args
+        nu = nu0 if nu is None else nu
+        e_min = e_min0 if e_min is None else e_min
+        e_max = e_max0 if e_max is None else e_max
+        exponent = exponent0 if exponent is None else exponent
+        self._mat_args = (kind, nu, e_min, e_max, exponent)
+        pix = (c_int64 * 3)(*(list(field.shape) + [0] * (3 - len(field.shape))))
+        if self.io == "host":
+            self._field = _f64(field).reshape(-1)
+            fptr = self._field.ctypes.data_as(POINTER(c_double))
+        else:
+            self._field = field
+            fptr = ctypes.cast(c_void_p(field.data_ptr()), POINTER(c_double))
+        mat = JfftMaterial(MATERIAL[kind], fptr, nu, e_min, e_max, exponent)
+        self._check(self.lib.jfft_set_material_coarse(self.h, ctypes.byref(mat), pix))
 
     def set_io_memory(self, io):
         self._check(self.lib.jfft_set_io_memory(self.h, MEM[io]))

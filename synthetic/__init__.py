@@ -13,4 +13,6 @@ from .fields import (  # noqa: F401
     random_field,
     mandel_unit_loads,
     mandel_dim,
+    circular_inclusion,
+    gaussian_filter,
 )

@@ -117,3 +117,23 @@ def random_field(shape, seed: int, zero_mean: bool = False) -> np.ndarray:
         axes = tuple(range(1, a.ndim))
         a = a - a.mean(axis=axes, keepdims=True)
     return a
+
+
+def circular_inclusion(shape, radius: float = 0.25, soft: float = 1e-4, hard: float = 1.0) -> np.ndarray:
+    """Compliant circular (2D) or spherical (3D) inclusion of the given radius (in cell
+    units, centred in the unit cell) in a stiff matrix, sampled at the nodes x = i / n:
+    `soft` inside, `hard` outside (the motivating example of Sec. 1)."""
+    shape = tuple(int(s) for s in shape)
+    axes = np.meshgrid(*[np.arange(n) / n - 0.5 for n in shape], indexing="ij")
+    r2 = sum(a * a for a in axes)
+    return np.where(r2 <= radius * radius, soft, hard).astype(np.float64)
+
+
+def gaussian_filter(rho: np.ndarray, times: int) -> np.ndarray:
+    """`times` periodic convolutions with the separable kernel [1 2 1] / 4 on every axis
+    (in 2D G = 1/16 [1 2 1]^T [1 2 1], Sec. 1)."""
+    out = np.asarray(rho, dtype=np.float64).copy()
+    for _ in range(int(times)):
+        for ax in range(out.ndim):
+            out = 0.25 * (np.roll(out, 1, ax) + 2.0 * out + np.roll(out, -1, ax))
+    return out

@@ -219,6 +219,48 @@ def test_iteration_counts_256_benchmark_density(contrast, pc):
         assert out["rel_res"][g] <= 1e-8 * 1.01
 
 
+@pytest.mark.parametrize("filt", [0, 4, 16])
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+def test_filtered_inclusion_counts(filt, pc):
+    """Sec. 1 motivating example at 128^2 (circular inclusion, contrast 1e4, filtered
+    `filt` times): iteration counts within one of the oracle's range over two summation
+    orders, true residual below the tolerance."""
+    from synthetic import circular_inclusion, gaussian_filter
+    from paper_2508_02613_gb300.jfft import Solver
+    shape = (128, 128)
+    rho = gaussian_filter(circular_inclusion(shape), filt)
+    s = Solver(shape, rho, 0.3)
+    out = s.solve(mandel_unit_loads(2)[:1], 1e-6, pc, want_stress=False)
+    prob = osolve.setup(shape, rho, 0.3)
+    a = osolve.solve(prob, mandel_unit_loads(2)[:1], 1e-6, pc)
+    b = osolve.solve(prob, mandel_unit_loads(2)[:1], 1e-6, pc, dot_order="sequential")
+    lo = min(int(a.iters[0]), int(b.iters[0])) - 1
+    hi = max(int(a.iters[0]), int(b.iters[0])) + 1
+    assert lo <= int(out["iters"][0]) <= hi, (int(out["iters"][0]), a.iters, b.iters)
+    assert out["rel_res"][0] <= 1e-6 * 1.01
+
+
+@pytest.mark.parametrize("p,n", [((4, 4), (16, 16)), ((8, 2), (32, 16)), ((4, 4, 2), (8, 16, 8))])
+def test_coarse_geometry_upsampling(p, n):
+    """jfft_set_material_coarse (geometry G_p on T_n) equals jfft_set_material with the
+    oracle's upsampled field, bit for bit."""
+    from oracle import material as omat
+    from paper_2508_02613_gb300.jfft import Solver
+    rng = np.random.default_rng(sum(p))
+    coarse = rng.uniform(0.0, 1.0, p)
+    fine = omat.upsample(coarse, n)
+    a = Solver(n, np.ones(n), 0.3, kind="density", e_min=1e-3, e_max=1.0, exponent=2.0)
+    a.set_material_coarse(coarse)
+    b = Solver(n, fine, 0.3, kind="density", e_min=1e-3, e_max=1.0, exponent=2.0)
+    assert np.array_equal(a.get_material(), b.get_material())
+    d = len(n)
+    oa = a.solve(mandel_unit_loads(d), 1e-10, "green_jacobi")
+    ob = b.solve(mandel_unit_loads(d), 1e-10, "green_jacobi")
+    assert np.array_equal(oa["u"], ob["u"]) and np.array_equal(oa["iters"], ob["iters"])
+    with pytest.raises(Exception):
+        a.set_material_coarse(rng.uniform(0.0, 1.0, tuple(2 * k for k in n)))
+
+
 @pytest.mark.parametrize("shape,normal,tangent", [((32, 8), [0, 2], [1]), ((16, 4, 4), [0, 4, 5], [1, 2, 3])])
 def test_laminate_closed_form(shape, normal, tangent):
     from tests.test_oracle_homogenisation import _laminate_C_hom

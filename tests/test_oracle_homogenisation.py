@@ -47,6 +47,25 @@ def test_laminate_matches_closed_form(shape, normal, tangent, pc):
     assert np.abs(out.C_hom - want).max() <= 1e-11 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("p,n", [(4, 16), (8, 32), (2, 8)])
+def test_coarse_geometry_on_a_finer_grid(p, n):
+    """Geometry G_p on T_n (Sec. 4, n >= p): every voxel takes its pixel's value, so a
+    laminate of p layers keeps the lamination formula of p equally thick layers on
+    every finer grid."""
+    rng = np.random.default_rng(p * n)
+    layers = 10.0 ** rng.uniform(-2, 0, p)
+    coarse = np.repeat(layers[:, None], p, axis=1)           # G_p, layers normal to e_1
+    fine = material.upsample(coarse, (n, n))
+    # brute force: voxel (i, j) belongs to pixel (i // (n/p), j // (n/p))
+    r = n // p
+    want_fine = np.array([[coarse[i // r, j // r] for j in range(n)] for i in range(n)])
+    assert np.array_equal(fine, want_fine)
+    prob = solve.setup((n, n), fine, 0.3)
+    out = solve.solve(prob, mandel_unit_loads(2), 1e-13, "green_jacobi")
+    want = _laminate_C_hom([e * fe.C_unit(2, 0.3) for e in layers], [0, 2], [1])
+    assert np.abs(out.C_hom - want).max() <= 1e-11 * np.abs(want).max()
+
+
 @pytest.mark.parametrize("shape", [(16, 16), (6, 6, 6)])
 def test_hill_bounds_symmetry_and_energy(shape):
     """Reuss <= C_hom <= Voigt (Loewner order), C_hom symmetric, and the macroscopic energy

@@ -133,3 +133,25 @@ def test_dot_order_rounding_floor():
         ua, ub = post.remove_mean(a.x), post.remove_mean(b.x)
         assert np.linalg.norm(ua - exact) <= 10 * tol * nrm
         assert np.linalg.norm(ua - ub) <= 10 * tol * nrm
+
+
+def test_filtered_inclusion_trend():
+    """The motivating example of Sec. 1 (compliant circular inclusion, contrast 1e4,
+    repeated [1 2 1]/4 filtering): with the sharp interface Green needs fewer iterations
+    than Green-Jacobi; after smoothing Green needs many more and Green-Jacobi fewer.
+    Qualitative (the paper plots the trend on 256^2, no counts are printed)."""
+    from oracle import assemble, solve
+    from synthetic import circular_inclusion, gaussian_filter
+    shape = (64, 64)
+    rho0 = circular_inclusion(shape)
+    its = {}
+    for i in (0, 8):
+        rho = gaussian_filter(rho0, i)
+        prob = solve.setup(shape, rho, 0.3)
+        f = assemble.assemble_rhs(shape, rho, prob.C, np.eye(3)[0])
+        its[i] = {pc: pcg.pcg(prob.apply_K, prob.minv(pc), f, 1e-6, 100000).iters
+                  for pc in ("green", "green_jacobi")}
+    assert its[0]["green"] < its[0]["green_jacobi"]
+    assert its[8]["green_jacobi"] < its[8]["green"]
+    assert its[8]["green"] > 5 * its[0]["green"]
+    assert its[8]["green_jacobi"] < its[0]["green_jacobi"]
