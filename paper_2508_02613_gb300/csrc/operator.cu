@@ -221,13 +221,17 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
 constexpr int kWarpStride = 31;
 constexpr int kWarpsPerCta2d = 4;
 
-template <typename T, int DOT, bool HAS_E>
+// HAS_X = false: x = 0 (right-hand side); SHIFT: the load's macroscopic strain is added
+// to the element modes; the output is sgn * (K x + K_shift).
+template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT>
 __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
     k_apply_K2d(Grid g, ElemConstT<T> ec, const T* __restrict__ E, T e_uniform, const T* __restrict__ x,
-                T* __restrict__ y, int64_t fstride, int seg, int groups, double* __restrict__ partial,
-                CgState* __restrict__ cg, StageCtl sc) {
+                T* __restrict__ y, int64_t fstride, int seg, int groups, const StrainShift* __restrict__ shifts,
+                T sgn, double* __restrict__ partial, CgState* __restrict__ cg, StageCtl sc) {
   const int b = blockIdx.z;
   if (cg && cg[b].done) return;
+  StrainShift sh;
+  if (SHIFT) sh = shifts[b];
   const int n0 = g.n[0], n1 = g.n[1];
   const int lane = threadIdx.x & 31;
   const int grp = blockIdx.x * kWarpsPerCta2d + (threadIdx.x >> 5);
@@ -249,12 +253,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
       const int rown = L0 % n0;
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        lo[a] = xb[a * g.N + (int64_t)row * n1 + c];
-        const T hlo = lane == 31 ? xb[a * g.N + (int64_t)row * n1 + cr] : T(0);
+        lo[a] = HAS_X ? xb[a * g.N + (int64_t)row * n1 + c] : T(0);
+        const T hlo = (HAS_X && lane == 31) ? xb[a * g.N + (int64_t)row * n1 + cr] : T(0);
         rlo[a] = __shfl_down_sync(0xffffffffu, lo[a], 1);
         if (lane == 31) rlo[a] = hlo;
-        nx[a] = xb[a * g.N + (int64_t)rown * n1 + c];
-        nh[a] = lane == 31 ? xb[a * g.N + (int64_t)rown * n1 + cr] : T(0);
+        nx[a] = HAS_X ? xb[a * g.N + (int64_t)rown * n1 + c] : T(0);
+        nh[a] = (HAS_X && lane == 31) ? xb[a * g.N + (int64_t)rown * n1 + cr] : T(0);
         carry[a] = T(0);
       }
       if (HAS_E) En = E[(int64_t)row * n1 + c];
@@ -270,10 +274,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
       if (e0 + 1 < L0 + seg) {           // prefetch node row e0 + 2 and element row e0 + 1
         const int rn2 = (e0 + 2) & (n0 - 1);   // n0 is a power of two
         const int re1 = (e0 + 1) & (n0 - 1);
+        if (HAS_X) {
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          nx[a] = xb[a * g.N + (int64_t)rn2 * n1 + c];
-          nh[a] = lane == 31 ? xb[a * g.N + (int64_t)rn2 * n1 + cr] : T(0);
+          for (int a = 0; a < 2; ++a) {
+            nx[a] = xb[a * g.N + (int64_t)rn2 * n1 + c];
+            nh[a] = lane == 31 ? xb[a * g.N + (int64_t)rn2 * n1 + cr] : T(0);
+          }
         }
         if (HAS_E) En = E[(int64_t)re1 * n1 + c];
       }
@@ -285,13 +291,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
         u[a][2] = hi[a];   // corner (1, 0): node (e0 + 1, c)
         u[a][3] = rhi[a];  // corner (1, 1): node (e0 + 1, c + 1)
       }
-      element_force<2, T, false>(ec, nullptr, u, Ee);
+      element_force<2, T, SHIFT>(ec, &sh, u, Ee);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const T from_left_lo = __shfl_up_sync(0xffffffffu, u[a][1], 1);
         const T from_left_hi = __shfl_up_sync(0xffffffffu, u[a][3], 1);
         if (e0 >= L0 && writer) {
-          const T q = carry[a] + u[a][0] + from_left_lo;
+          const T q = sgn * (carry[a] + u[a][0] + from_left_lo);
           yb[a * g.N + (int64_t)e0 * n1 + ocol] = q;
           if (DOT == 1) dot += lo[a] * q;
           if (DOT == 2) dot += q * q;
@@ -309,19 +315,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
   }
 }
 
-template <typename T, int DOT, bool HAS_E>
+template <typename T, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false>
 static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x, T* y, int nb,
                                int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
-                               StageCtl sc) {
+                               StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
   const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
   const int ctas_x = (groups + kWarpsPerCta2d - 1) / kWarpsPerCta2d;
   int seg = std::min(g.n[0], 16);
   while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
   dim3 grid(ctas_x, g.n[0] / seg, nb);
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
-                                    : (DOT == 1 ? "apply_K" : (HAS_E ? "apply_K_plain" : "apply_K_ref"));
-  JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
-                       g, ec, E, e_uniform, x, y, fstride, seg, groups, partial, cg, sc));
+                     : DOT == 1 ? "apply_K"
+                     : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
+  JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+                       g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
@@ -368,10 +375,19 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
                              double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, int dot_mode,
                              double* partial, int* nparts, CgState* cg, cudaStream_t st, StageCtl sc) {
   const bool hx = x != nullptr, he = E != nullptr, sh = shifts != nullptr;
-  if (D == 2 && hx && !sh && sgn == 1.0 && dot_mode != 2) {
-    if (dot_mode == 1 && he) return apply_K2d_t<double, 1, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
-    if (dot_mode == 0 && he) return apply_K2d_t<double, 0, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
-    if (dot_mode == 0 && !he) return apply_K2d_t<double, 0, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
+  if (D == 2) {
+    if (hx && !sh && sgn == 1.0) {
+      if (dot_mode == 1 && he) return apply_K2d_t<double, 1, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
+      if (dot_mode == 0 && he) return apply_K2d_t<double, 0, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
+      if (dot_mode == 0 && !he) return apply_K2d_t<double, 0, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc);
+    }
+    // right-hand side (x = 0) and true residual, with the strain shift, ||y||^2 or none
+    if (he && sh && (dot_mode == 2 || dot_mode == 0)) {
+      if (!hx && dot_mode == 2) return apply_K2d_t<double, 2, true, false, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc, shifts, sgn);
+      if (!hx && dot_mode == 0) return apply_K2d_t<double, 0, true, false, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc, shifts, sgn);
+      if (hx && dot_mode == 2) return apply_K2d_t<double, 2, true, true, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc, shifts, sgn);
+      if (hx && dot_mode == 0) return apply_K2d_t<double, 0, true, true, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc, shifts, sgn);
+    }
   }
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \

