@@ -37,11 +37,11 @@ def element_dofs(n) -> np.ndarray:
     return np.concatenate([node_of_corner + alpha * N for alpha in range(d)], axis=1)
 
 
-def assemble_K(n, E: np.ndarray, C: np.ndarray) -> sp.csr_matrix:
+def assemble_K(n, E: np.ndarray, C: np.ndarray, element: str = "q1") -> sp.csr_matrix:
     """Sparse K = sum_e E_e P_e^T A P_e, A the element matrix of material ``C``."""
     n = tuple(int(k) for k in n)
     d = len(n)
-    A = fe.element_matrix(d, grid_spacing(n), C)
+    A = fe.element_matrix(d, grid_spacing(n), C, element)
     g = element_dofs(n)
     ne, nl = g.shape
     rows = np.repeat(g, nl, axis=1).reshape(-1)
@@ -53,11 +53,11 @@ def assemble_K(n, E: np.ndarray, C: np.ndarray) -> sp.csr_matrix:
     return K
 
 
-def assemble_rhs(n, E: np.ndarray, C: np.ndarray, eps_bar: np.ndarray) -> np.ndarray:
+def assemble_rhs(n, E: np.ndarray, C: np.ndarray, eps_bar: np.ndarray, element: str = "q1") -> np.ndarray:
     """f = -sum_e E_e P_e^T b(eps_bar), b = sum_q w_q B_q^T C eps_bar. Shape [d, *n]."""
     n = tuple(int(k) for k in n)
     d = len(n)
-    b = fe.element_strain_load(d, grid_spacing(n), C, np.asarray(eps_bar, dtype=np.float64))
+    b = fe.element_strain_load(d, grid_spacing(n), C, np.asarray(eps_bar, dtype=np.float64), element)
     g = element_dofs(n)
     vals = -(np.asarray(E, dtype=np.float64).reshape(-1)[:, None] * b[None, :])
     f = np.zeros(d * int(np.prod(n)))

@@ -108,23 +108,66 @@ def C_unit(d: int, nu: float) -> np.ndarray:
     return isotropic_C(d, *lame_from_young(1.0, nu))
 
 
-def element_matrix(d: int, h, C: np.ndarray) -> np.ndarray:
-    """A = sum_q w_q B_q^T C B_q with w_q the Gauss weights times the element volume."""
-    pts, w = gauss_points(d)
-    vol = float(np.prod(h))
+ELEMENTS = ("q1", "p1")
+
+
+def _mandel_from_gradients(grad: np.ndarray) -> np.ndarray:
+    """Mandel symmetrised-gradient matrix (d* x d nc) from shape gradients [nc, d]."""
+    nc, d = grad.shape
+    B = np.zeros((d * (d + 1) // 2, d * nc))
+    for m, (i, j) in enumerate(mandel_pairs(d)):
+        for c in range(nc):
+            if i == j:
+                B[m, i * nc + c] += grad[c, i]
+            else:
+                s = 1.0 / math.sqrt(2.0)
+                B[m, i * nc + c] += s * grad[c, j]
+                B[m, j * nc + c] += s * grad[c, i]
+    return B
+
+
+def triangle_pair_B(h):
+    """The P1 discretisation of a 2D voxel (Sec. 4 "Discretization": linear triangles):
+    the voxel with corners (o0, o1) in {0,1}^2 is split along the diagonal from (0, 0)
+    to (1, 1) into T1 = {(0,0), (1,0), (1,1)} and T2 = {(0,0), (1,1), (0,1)}. Each
+    triangle has a constant strain; returns [B_T1, B_T2] on the voxel's 4 corners (the
+    corner outside the triangle has zero columns) and the two weights (area h0 h1 / 2)."""
+    h0, h1 = float(h[0]), float(h[1])
+    # corner order of corners(2): (0,0), (0,1), (1,0), (1,1)
+    g1 = np.array([[-1.0 / h0, 0.0], [0.0, 0.0], [1.0 / h0, -1.0 / h1], [0.0, 1.0 / h1]])
+    g2 = np.array([[0.0, -1.0 / h1], [-1.0 / h0, 1.0 / h1], [0.0, 0.0], [1.0 / h0, 0.0]])
+    area = 0.5 * h0 * h1
+    return [_mandel_from_gradients(g1), _mandel_from_gradients(g2)], [area, area]
+
+
+def element_points(d: int, h, element: str = "q1"):
+    """Integration points of one voxel: the matrices B_q and weights w_q (sum = voxel
+    volume) with K_e = sum_q w_q B_q^T C B_q. Q1: the 2^d Gauss points; P1 (2D): the two
+    constant-strain triangles."""
+    if element == "q1":
+        pts, w = gauss_points(d)
+        vol = float(np.prod(h))
+        return [mandel_B(d, xi, h) for xi in pts], [wq * vol for wq in w]
+    if element == "p1":
+        if d != 2:
+            raise ValueError("P1 triangles are 2D")
+        return triangle_pair_B(h)
+    raise ValueError(element)
+
+
+def element_matrix(d: int, h, C: np.ndarray, element: str = "q1") -> np.ndarray:
+    """A = sum_q w_q B_q^T C B_q over the voxel's integration points (element_points)."""
+    Bs, ws = element_points(d, h, element)
     A = np.zeros((d * 2 ** d, d * 2 ** d))
-    for xi, wq in zip(pts, w):
-        B = mandel_B(d, xi, h)
-        A += (wq * vol) * (B.T @ C @ B)
+    for B, wq in zip(Bs, ws):
+        A += wq * (B.T @ C @ B)
     return A
 
 
-def element_strain_load(d: int, h, C: np.ndarray, eps: np.ndarray) -> np.ndarray:
+def element_strain_load(d: int, h, C: np.ndarray, eps: np.ndarray, element: str = "q1") -> np.ndarray:
     """b = sum_q w_q B_q^T C eps for a constant Mandel strain ``eps`` (element part of f)."""
-    pts, w = gauss_points(d)
-    vol = float(np.prod(h))
+    Bs, ws = element_points(d, h, element)
     b = np.zeros(d * 2 ** d)
-    for xi, wq in zip(pts, w):
-        B = mandel_B(d, xi, h)
-        b += (wq * vol) * (B.T @ (C @ eps))
+    for B, wq in zip(Bs, ws):
+        b += wq * (B.T @ (C @ eps))
     return b

@@ -36,11 +36,11 @@ import numpy as np
 from . import assemble
 
 
-def impulse_responses(n, C_ref: np.ndarray) -> np.ndarray:
+def impulse_responses(n, C_ref: np.ndarray, element: str = "q1") -> np.ndarray:
     """Step 1 of Alg. 1: R[alpha, beta, *n] = (K_ref e_{alpha, node 0})_beta."""
     n = tuple(int(k) for k in n)
     d = len(n)
-    K_ref = assemble.assemble_K(n, np.ones(n), C_ref)
+    K_ref = assemble.assemble_K(n, np.ones(n), C_ref, element)
     R = np.zeros((d, d) + n)
     for alpha in range(d):
         imp = np.zeros((d,) + n)
@@ -74,11 +74,11 @@ def _reflect(x: np.ndarray, axes) -> np.ndarray:
     return np.roll(np.flip(x, axes), 1, axes)
 
 
-def green_symbol(n, C_ref: np.ndarray, explicit_dft: bool = False):
+def green_symbol(n, C_ref: np.ndarray, explicit_dft: bool = False, element: str = "q1"):
     """Steps 2-3 of Alg. 1. Returns (K_hat, G_hat), each real [d, d, *n]."""
     n = tuple(int(k) for k in n)
     d = len(n)
-    R = impulse_responses(n, C_ref)
+    R = impulse_responses(n, C_ref, element)
     axes = tuple(range(2, 2 + d))
     K_c = _transform(R, axes, False, explicit_dft)
     K_hat = 0.5 * (K_c + _reflect(K_c, axes)).real

@@ -21,32 +21,32 @@ def remove_mean(u: np.ndarray) -> np.ndarray:
     return u - u.mean(axis=axes, keepdims=True)
 
 
-def gauss_point_stress(n, E: np.ndarray, C: np.ndarray, eps_bar: np.ndarray, u: np.ndarray):
-    """sigma[q, e, :] for every Gauss point q and element e (Mandel), and the weights."""
+def gauss_point_stress(n, E: np.ndarray, C: np.ndarray, eps_bar: np.ndarray, u: np.ndarray,
+                       element: str = "q1"):
+    """sigma[q, e, :] at every integration point q of every voxel e (Mandel: the Gauss
+    points for Q1, the two triangles for P1), and the weights."""
     n = tuple(int(k) for k in n)
     d = len(n)
     h = assemble.grid_spacing(n)
     g = assemble.element_dofs(n)
     ue = u.reshape(-1)[g]  # [N_el, d 2^d]
-    pts, w = fe.gauss_points(d)
-    vol = float(np.prod(h))
+    Bs, ws = fe.element_points(d, h, element)
     Ef = np.asarray(E, dtype=np.float64).reshape(-1)
     sig = []
-    for xi in pts:
-        B = fe.mandel_B(d, xi, h)
+    for B in Bs:
         eps = eps_bar[None, :] + ue @ B.T
         sig.append(Ef[:, None] * (eps @ C.T))
-    return np.stack(sig), np.array(w) * vol
+    return np.stack(sig), np.array(ws)
 
 
-def element_stress(n, E, C, eps_bar, u) -> np.ndarray:
-    """Element-averaged Mandel stress, shape [d*, *n]."""
+def element_stress(n, E, C, eps_bar, u, element: str = "q1") -> np.ndarray:
+    """Voxel-averaged Mandel stress (equal-weight points), shape [d*, *n]."""
     n = tuple(int(k) for k in n)
-    sig, _ = gauss_point_stress(n, E, C, eps_bar, u)
+    sig, _ = gauss_point_stress(n, E, C, eps_bar, u, element)
     return sig.mean(axis=0).T.reshape((sig.shape[2],) + n)
 
 
-def homogenised_stress(n, E, C, eps_bar, u) -> np.ndarray:
-    """(1/|Y|) int sigma dx by the Gauss rule, |Y| = 1: Mandel vector of length d*."""
-    sig, w = gauss_point_stress(n, E, C, eps_bar, u)
+def homogenised_stress(n, E, C, eps_bar, u, element: str = "q1") -> np.ndarray:
+    """(1/|Y|) int sigma dx by the voxel rule, |Y| = 1: Mandel vector of length d*."""
+    sig, w = gauss_point_stress(n, E, C, eps_bar, u, element)
     return np.einsum("q,qes->s", w, sig)

@@ -36,6 +36,7 @@ class CellProblem:
     G_hat: np.ndarray
     diag: np.ndarray
     J_half: np.ndarray
+    element: str = "q1"
 
     @property
     def d(self):
@@ -57,18 +58,20 @@ class CellProblem:
 
 
 def setup(n, E: np.ndarray, nu: float, C_ref: np.ndarray | None = None,
-          void_replacement: float = 1.0) -> CellProblem:
+          void_replacement: float = 1.0, element: str = "q1") -> CellProblem:
+    """``element``: "q1" (bilinear / trilinear voxels, full Gauss rule) or "p1" (2D: each
+    voxel split into two linear triangles, fe.triangle_pair_B)."""
     n = tuple(int(k) for k in n)
     d = len(n)
     E = np.asarray(E, dtype=np.float64).reshape(n)
     C = fe.C_unit(d, nu)
-    K = assemble.assemble_K(n, E, C)
+    K = assemble.assemble_K(n, E, C, element)
     if C_ref is None:
         C_ref = float(E.mean()) * C
-    _, G_hat = green.green_symbol(n, C_ref)
+    _, G_hat = green.green_symbol(n, C_ref, element=element)
     diag = jacobi.diag_assembled(K, (d,) + n)
     J_half = jacobi.jacobi_half(diag, void_replacement)
-    return CellProblem(n, E, nu, C, K, G_hat, diag, J_half)
+    return CellProblem(n, E, nu, C, K, G_hat, diag, J_half, element)
 
 
 @dataclass
@@ -91,7 +94,7 @@ def solve(prob: CellProblem, eps_bar: np.ndarray, tol: float, precond: str,
     us, raws, stresses, chom, its, rres = [], [], [], [], [], []
     minv = prob.minv(precond)
     for g in range(nl):
-        f = assemble.assemble_rhs(prob.n, prob.E, prob.C, eps_bar[g])
+        f = assemble.assemble_rhs(prob.n, prob.E, prob.C, eps_bar[g], prob.element)
         if fixed_iters is not None:
             res = pcg.pcg(prob.apply_K, minv, f, 0.0, int(fixed_iters[g]), "rel", dot_order)
         else:
@@ -102,8 +105,8 @@ def solve(prob: CellProblem, eps_bar: np.ndarray, tol: float, precond: str,
         rr = np.linalg.norm(f - prob.apply_K(u)) / nf if nf > 0 else 0.0
         us.append(u)
         raws.append(raw)
-        stresses.append(post.element_stress(prob.n, prob.E, prob.C, eps_bar[g], u))
-        chom.append(post.homogenised_stress(prob.n, prob.E, prob.C, eps_bar[g], u))
+        stresses.append(post.element_stress(prob.n, prob.E, prob.C, eps_bar[g], u, prob.element))
+        chom.append(post.homogenised_stress(prob.n, prob.E, prob.C, eps_bar[g], u, prob.element))
         its.append(res.iters)
         rres.append(rr)
     return SolveResult(np.stack(us), np.stack(stresses), np.stack(chom, axis=1),

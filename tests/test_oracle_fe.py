@@ -98,3 +98,64 @@ def test_mandel_shear_convention():
     m = np.array([eps_t[i, j] * (1 if i == j else math.sqrt(2)) for i, j in pairs])
     assert math.isclose(m[5], g["mandel_component_6"], rel_tol=1e-15)
     assert math.isclose(m @ m, np.sum(eps_t * eps_t), rel_tol=1e-15)
+
+
+# ---- P1 triangles (each voxel split along the (0,0)-(1,1) diagonal) ----------------
+
+def test_p1_patch_test_and_energy():
+    """Both triangles reproduce the exact constant strain of any affine displacement, and
+    the voxel energy equals vol * eps : C : eps (patch test)."""
+    h = (0.25, 0.125)
+    rng = np.random.default_rng(3)
+    Gm = rng.standard_normal((2, 2))
+    xs = [np.array([o[0] * h[0], o[1] * h[1]]) for o in fe.corners(2)]
+    ue = np.concatenate([[(Gm @ x)[a] for x in xs] for a in range(2)])
+    eps_t = 0.5 * (Gm + Gm.T)
+    want = np.array([eps_t[0, 0], eps_t[1, 1], np.sqrt(2.0) * eps_t[0, 1]])
+    Bs, ws = fe.element_points(2, h, "p1")
+    assert len(Bs) == 2 and np.isclose(sum(ws), h[0] * h[1])
+    for B in Bs:
+        assert np.allclose(B @ ue, want, atol=1e-13)
+    C = fe.C_unit(2, 0.3)
+    A = fe.element_matrix(2, h, C, "p1")
+    assert np.isclose(ue @ A @ ue, h[0] * h[1] * want @ C @ want, rtol=1e-13)
+
+
+def test_p1_voxel_matrix_rigid_modes_and_rank():
+    A = fe.element_matrix(2, (0.5, 0.5), fe.C_unit(2, 0.25), "p1")
+    assert np.abs(A - A.T).max() < 1e-13
+    w = np.linalg.eigvalsh(A)
+    assert w.min() > -1e-12 * w.max()
+    assert np.sum(np.abs(w) < 1e-10 * w.max()) == 3     # two translations and a rotation
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (8, 4)])
+def test_p1_global_operator_kernel(shape):
+    """The periodic P1 stiffness is symmetric PSD with exactly the d translations as kernel."""
+    from oracle import assemble
+    E = np.random.default_rng(1).uniform(0.5, 2.0, shape)
+    K = assemble.assemble_K(shape, E, fe.C_unit(2, 0.3), "p1").toarray()
+    assert np.abs(K - K.T).max() < 1e-12
+    w = np.linalg.eigvalsh(K)
+    assert w.min() > -1e-10 * w.max()
+    assert np.sum(np.abs(w) < 1e-9 * w.max()) == 2
+
+
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+def test_p1_laminate_and_homogeneous_cell(pc):
+    """Layers normal to e_1: the exact solution is piecewise linear in x_1 with kinks on
+    grid lines, so P1 reproduces the lamination formula; a uniform cell under a random
+    zero-mean load converges in one Green iteration."""
+    from oracle import assemble, pcg, solve
+    from synthetic import laminate_density, mandel_unit_loads, random_field
+    from tests.test_oracle_homogenisation import _laminate_C_hom
+    shape = (16, 8)
+    rho = laminate_density(shape, 1e2)
+    prob = solve.setup(shape, rho, 0.3, element="p1")
+    out = solve.solve(prob, mandel_unit_loads(2), 1e-13, pc)
+    layers = rho.reshape(shape[0], -1)[:, 0]
+    want = _laminate_C_hom([e * fe.C_unit(2, 0.3) for e in layers], [0, 2], [1])
+    assert np.abs(out.C_hom - want).max() <= 1e-11 * np.abs(want).max()
+    uni = solve.setup((8, 8), np.full((8, 8), 2.5), 0.3, element="p1")
+    f = random_field((2, 8, 8), 4, zero_mean=True)
+    assert pcg.pcg(uni.apply_K, uni.minv(pc), f, 1e-12, 50).iters == 1
