@@ -71,6 +71,11 @@ typedef enum {
 } jfft_material_kind;
 
 typedef enum {
+  JFFT_ELEM_Q1 = 0,          /* bilinear (2D) / trilinear (3D) voxel, full 2^d Gauss rule */
+  JFFT_ELEM_P1 = 1           /* 2D: two linear triangles per voxel (the paper's Sec. 4 discretisation) */
+} jfft_element;
+
+typedef enum {
   JFFT_PREC_FP64 = 0,        /* every step in FP64 */
   JFFT_PREC_MIXED = 1        /* FP64 iterative refinement around an FP32 PCG: operator, FFT, preconditioner and
                                 vectors of the inner solve in FP32, CG scalars and every reduction above the
@@ -119,6 +124,9 @@ typedef struct {
   int graphs;                /* 1 (default): the check_every-iteration PCG chunk is captured once as a
                                 CUDA graph and replayed; 0: every kernel is launched from the host.
                                 Results are identical; graphs are not used while profiling is on. */
+  int element;               /* voxel discretisation: JFFT_ELEM_Q1 (default, bilinear / trilinear, full
+                                Gauss rule) or JFFT_ELEM_P1 (2D only: each voxel split along its
+                                (0,0)-(1,1) diagonal into two linear triangles, Sec. 4) */
 } jfft_options;
 
 typedef struct {

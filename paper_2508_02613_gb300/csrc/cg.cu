@@ -131,7 +131,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__ r, T* __restrict__ z, int64_t stride,
                                                    const T* __restrict__ js, double3 jscale, double void_js,
                                                    int identity, CgState* __restrict__ cg,
-                                                   double* __restrict__ partial, StageCtl sc) {
+                                                   double* __restrict__ partial, StageCtl sc, int64_t jcs) {
   const int b = blockIdx.y;
   if (cg && cg[b].done) return;
   const int64_t off = (int64_t)b * stride;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__
     T zv = rv;
     if (!identity) {
       const int a = (int)(i / g.N);
-      const T s = js[i - a * g.N];
+      const T s = js[i - a * g.N + a * jcs];
       const T ka = (T)(a == 0 ? jscale.x : (a == 1 ? jscale.y : jscale.z));
       const T jh = s > T(0) ? s * ka : (T)void_js;
       zv = jh * jh * rv;
@@ -157,24 +157,24 @@ __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__
 
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
                                   const double* jscale, double void_js, bool identity, double* partial, int* nparts,
-                                  CgState* done, cudaStream_t st, StageCtl sc) {
+                                  CgState* done, cudaStream_t st, StageCtl sc, int64_t jcs) {
   const int bl = vec_blocks(g.d * g.N / 2);
   JFFT_K("jacobi_pc", st,
          k_jacobi_pc<double><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
                                                            make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                                           identity ? 1 : 0, done, partial, sc));
+                                                           identity ? 1 : 0, done, partial, sc, jcs));
   *nparts = bl;
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
                                       const double* jscale, double void_js, bool identity, double* partial,
-                                      int* nparts, CgState* done, cudaStream_t st, StageCtl sc) {
+                                      int* nparts, CgState* done, cudaStream_t st, StageCtl sc, int64_t jcs) {
   const int bl = vec_blocks(g.d * g.N / 2);
   JFFT_K("jacobi_pc_f32", st,
          k_jacobi_pc<float><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
                                                           make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                                          identity ? 1 : 0, done, partial, sc));
+                                                          identity ? 1 : 0, done, partial, sc, jcs));
   *nparts = bl;
   return cudaGetLastError();
 }

@@ -150,6 +150,81 @@ template <int D> JFFT_HD void element_stress(const ElemConst& ec, const StrainSh
   }
 }
 
+// P1 discretisation of a 2D voxel (Sec. 4 "Discretization": linear triangles): the voxel
+// is split along the diagonal from corner (0,0) to corner (1,1) into T1 = {(0,0), (1,0),
+// (1,1)} and T2 = {(0,0), (1,1), (0,1)}, each with a constant strain. Corner index
+// c = o0 * 2 + o1. Stress of one triangle from its displacement gradient grad[a][b]
+// = du_a / dx_b plus the macroscopic strain (tensor form eb), for unit E.
+template <typename V> JFFT_HD void tri_stress(const ElemConstT<V>& ec, const V (*grad)[2], const V (*eb)[2], V (*sg)[2]) {
+  const V e00 = grad[0][0] + eb[0][0], e11 = grad[1][1] + eb[1][1];
+  const V e01 = V(0.5) * (grad[0][1] + grad[1][0]) + eb[0][1];
+  const V tr = e00 + e11;
+  sg[0][0] = ec.lam * tr + V(2) * ec.mu * e00;
+  sg[1][1] = ec.lam * tr + V(2) * ec.mu * e11;
+  sg[0][1] = sg[1][0] = V(2) * ec.mu * e01;
+}
+
+// Corner forces f[a][c] = E * K_voxel-unit u for the two triangles (in place), with an
+// optional macroscopic strain shift (StrainShift holds eps_ab / gs_b).
+template <typename V, bool SHIFT>
+JFFT_HD void tri_pair_force(const ElemConstT<V>& ec, const StrainShift* sh, V (*u)[4], V E) {
+  const V ih0 = V(2) * ec.gs[0], ih1 = V(2) * ec.gs[1];   // gs_a = 1 / (2 h_a) in 2D
+  const V area = V(0.5) * ec.vol;
+  V eb[2][2] = {{V(0), V(0)}, {V(0), V(0)}};
+  if (SHIFT) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) eb[a][b] = V(sh->s[a][b]) * ec.gs[b];
+  }
+  V g1[2][2], g2[2][2], s1[2][2], s2[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    g1[a][0] = (u[a][2] - u[a][0]) * ih0;   // T1: (0,0) -> (1,0) along axis 0
+    g1[a][1] = (u[a][3] - u[a][2]) * ih1;   //     (1,0) -> (1,1) along axis 1
+    g2[a][1] = (u[a][1] - u[a][0]) * ih1;   // T2: (0,0) -> (0,1) along axis 1
+    g2[a][0] = (u[a][3] - u[a][1]) * ih0;   //     (0,1) -> (1,1) along axis 0
+  }
+  tri_stress<V>(ec, g1, eb, s1);
+  tri_stress<V>(ec, g2, eb, s2);
+  const V w = area * E;
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    // T1 shape gradients: (0,0) (-ih0, 0), (1,0) (ih0, -ih1), (1,1) (0, ih1)
+    // T2 shape gradients: (0,0) (0, -ih1), (0,1) (-ih0, ih1), (1,1) (ih0, 0)
+    const V f0 = -ih0 * s1[a][0] - ih1 * s2[a][1];
+    const V f1 = -ih0 * s2[a][0] + ih1 * s2[a][1];
+    const V f2 = ih0 * s1[a][0] - ih1 * s1[a][1];
+    const V f3 = ih1 * s1[a][1] + ih0 * s2[a][0];
+    u[a][0] = w * f0;
+    u[a][1] = w * f1;
+    u[a][2] = w * f2;
+    u[a][3] = w * f3;
+  }
+}
+
+// Voxel-averaged Mandel stress E C (eps_bar + eps(u)) of the two triangles.
+JFFT_HD void tri_pair_stress(const ElemConst& ec, const StrainShift* sh, double (*u)[4], double E, double* sig) {
+  const double ih0 = 2.0 * ec.gs[0], ih1 = 2.0 * ec.gs[1];
+  double eb[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  if (sh)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) eb[a][b] = sh->s[a][b] * ec.gs[b];
+  double g1[2][2], g2[2][2], s1[2][2], s2[2][2];
+  for (int a = 0; a < 2; ++a) {
+    g1[a][0] = (u[a][2] - u[a][0]) * ih0;
+    g1[a][1] = (u[a][3] - u[a][2]) * ih1;
+    g2[a][1] = (u[a][1] - u[a][0]) * ih1;
+    g2[a][0] = (u[a][3] - u[a][1]) * ih0;
+  }
+  tri_stress<double>(ec, g1, eb, s1);
+  tri_stress<double>(ec, g2, eb, s2);
+  const double r2 = 1.4142135623730951;
+  sig[0] = E * 0.5 * (s1[0][0] + s2[0][0]);
+  sig[1] = E * 0.5 * (s1[1][1] + s2[1][1]);
+  sig[2] = E * r2 * 0.5 * (s1[0][1] + s2[0][1]);
+}
+
 // Constants of the unit-E element for a d-dimensional box h[0..d-1] and Lame pair.
 inline ElemConst make_elem_const(int d, const double* h, double lam, double mu) {
   ElemConst ec = {};
@@ -168,6 +243,7 @@ inline ElemConst make_elem_const(int d, const double* h, double lam, double mu) 
   ec.lam = lam;
   ec.mu = mu;
   ec.vol = vol;
+  ec.elem = 0;
   return ec;
 }
 

@@ -62,8 +62,9 @@ template <typename T> __host__ __device__ inline int lanes_per_line(int L) {
 }
 
 template <typename T> struct JScaleT {
-  T k[3];     // kappa_a^-1/2 per component
-  T void_js;  // J^1/2 at void nodes
+  T k[3];      // kappa_a^-1/2 per component
+  T void_js;   // J^1/2 at void nodes
+  int64_t cs;  // component stride of the node factors (0: one factor per node, N: one per DOF)
 };
 
 template <typename T> __device__ __forceinline__ T kscale(const JScaleT<T>& jsc, int a) {
@@ -115,8 +116,9 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
         x = reinterpret_cast<const C*>(rin + ((int64_t)S * R + row) * Lin)[m];
         if (JAC) {
           const int64_t node = row * Lin + 2 * m;
-          x.x *= jhalf<T>(js, ka, jsc.void_js, node);
-          x.y *= jhalf<T>(js, ka, jsc.void_js, node + 1);
+          const T* jsa = js + jsc.cs * (S % D);
+          x.x *= jhalf<T>(jsa, ka, jsc.void_js, node);
+          x.y *= jhalf<T>(jsa, ka, jsc.void_js, node + 1);
         }
       } else {
         x = cin[((int64_t)S * R + row) * Lin + m];
@@ -281,8 +283,9 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
       C x = res[line * ls + spad(m)];
       const int64_t node = row * n + 2 * m;
       if (JAC) {
-        x.x *= jhalf<T>(js, ka, jsc.void_js, node);
-        x.y *= jhalf<T>(js, ka, jsc.void_js, node + 1);
+        const T* jsa = js + jsc.cs * a;
+        x.x *= jhalf<T>(jsa, ka, jsc.void_js, node);
+        x.y *= jhalf<T>(jsa, ka, jsc.void_js, node + 1);
       }
       const int64_t off = ((int64_t)S * R + row) * n + 2 * m;
       reinterpret_cast<C*>(rout + off)[0] = x;
@@ -427,10 +430,11 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
 template <typename T>
 static cudaError_t green_precond_t(const Grid& g, const FftPlanT<T>& p, const T* r, T* z, int nb, const T* js,
                                    const double* jscale, double void_js, bool jacobi, double* partial, int* nparts,
-                                   CgState* done, cudaStream_t st, StageCtl sc) {
+                                   CgState* done, cudaStream_t st, StageCtl sc, int64_t jcs) {
   JScaleT<T> jsc;
   for (int a = 0; a < 3; ++a) jsc.k[a] = (T)jscale[a];
   jsc.void_js = (T)void_js;
+  jsc.cs = jcs;
   JFFT_TRY(pass_rows_real_fwd<T>(g, p, r, nb, jacobi, js, jsc, done, st));
   if (g.d == 3) JFFT_TRY(pass_rows_cplx_fwd<T>(g, p, nb, done, st));
   JFFT_TRY(pass_lines<T>(g, p, nb, true, done, st));
@@ -441,14 +445,15 @@ static cudaError_t green_precond_t(const Grid& g, const FftPlanT<T>& p, const T*
 cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
                                  int64_t /*field_stride*/, const double* js, const double* jscale, double void_js,
                                  bool jacobi, double* partial, int* nparts, CgState* done, cudaStream_t st,
-                                 StageCtl sc) {
-  return green_precond_t<double>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st, sc);
+                                 StageCtl sc, int64_t jcs) {
+  return green_precond_t<double>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st, sc, jcs);
 }
 
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
                                      const float* js, const double* jscale, double void_js, bool jacobi,
-                                     double* partial, int* nparts, CgState* done, cudaStream_t st, StageCtl sc) {
-  return green_precond_t<float>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st, sc);
+                                     double* partial, int* nparts, CgState* done, cudaStream_t st, StageCtl sc,
+                                     int64_t jcs) {
+  return green_precond_t<float>(g, p, r, z, nb, js, jscale, void_js, jacobi, partial, nparts, done, st, sc, jcs);
 }
 
 cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,

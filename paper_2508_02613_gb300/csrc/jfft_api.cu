@@ -29,6 +29,9 @@ struct jfft_solver {
   double cref_lam = 0.0, cref_mu = 0.0;
   double e_ref = 1.0;
   double kappa[3] = {0, 0, 0}, jscale[3] = {0, 0, 0}, void_js = 1.0;
+  int element = 0;                 // JFFT_ELEM_Q1 or JFFT_ELEM_P1
+  int64_t jcs = 0;                 // component stride of the J^1/2 node factors (P1: N)
+  double kappa_p1[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // P1: diagonal of the unit voxel, [corner][component]
   double scale_store = 1.0;
   // device workspace
   double *field = nullptr, *E = nullptr, *esum = nullptr, *js = nullptr, *G = nullptr;
@@ -251,6 +254,7 @@ extern "C" void jfft_default_options(jfft_options* o) {
   o->inner_tol = 1e-3;
   o->max_refine = 30;
   o->graphs = 1;
+  o->element = JFFT_ELEM_Q1;
 }
 
 static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
@@ -325,12 +329,12 @@ static jfft_status build_symbol(jfft_solver* h) {
 }
 
 // Device workspace of a solver (bytes), as allocated by jfft_create.
-static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision) {
+static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int element = 0) {
   const int d = g.d;
   const int64_t fe = (int64_t)d * g.N;
   const int64_t spec_n = (int64_t)nbmax * d * g.F;
   size_t total = 0;
-  total += 4 * g.N * sizeof(double);                               // field, E, esum, js
+  total += (4 + (element == 1 ? 1 : 0)) * g.N * sizeof(double);   // field, E, esum, js (per DOF for P1)
   total += (size_t)g.F * ds * sizeof(double);                       // G
   for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(double2);
   total += (size_t)spec_n * sizeof(double2) * (d == 3 ? 2 : 1);     // T (U)
@@ -339,7 +343,7 @@ static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision) {
   total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int) + sizeof(unsigned));
   total += sizeof(int);                                             // chunk counter
   if (precision == JFFT_PREC_MIXED) {
-    total += 2 * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
+    total += (2 + (element == 1 ? 1 : 0)) * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
     for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
     total += (size_t)spec_n * sizeof(float2) * (d == 3 ? 2 : 1);
     total += 5 * (size_t)nbmax * fe * sizeof(float);
@@ -381,7 +385,20 @@ static void set_unit_material(jfft_solver* h, double nu) {
   double hh[3];
   for (int a = 0; a < d; ++a) hh[a] = 1.0 / g.n[a];
   h->ec = make_elem_const(d, hh, lam_u, mu_u);
+  h->ec.elem = h->element;
   for (int a = 0; a < 3; ++a) h->kappa[a] = 1.0;
+  if (h->element == JFFT_ELEM_P1) {
+    // corner-dependent diagonal of the two-triangle voxel; the node factors carry it all
+    for (int c = 0; c < 4; ++c)
+      for (int a = 0; a < 2; ++a) {
+        double u[2][4] = {};
+        u[a][c] = 1.0;
+        tri_pair_force<double, false>(h->ec, nullptr, u, 1.0);
+        h->kappa_p1[c * 2 + a] = u[a][c];
+      }
+    for (int a = 0; a < 3; ++a) h->jscale[a] = 1.0;
+    return;
+  }
   for (int a = 0; a < d; ++a) {
     if (d == 2) {
       double u[2][4] = {};
@@ -445,7 +462,12 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   }
   CK(launch_material(h->field, h->E, g.N, m->kind, m->e_min, m->e_max, m->exponent, h->st));
   CK(launch_node_esum(g, h->E, h->esum, h->st));
-  CK(launch_jacobi_half(h->esum, h->js, g.N, h->st));
+  if (h->element == JFFT_ELEM_P1) {
+    CK(launch_diag_p1(g, h->E, h->kappa_p1, h->x, h->st));   // x is free outside a solve
+    CK(launch_jacobi_half(h->x, h->js, 2 * g.N, h->st));
+  } else {
+    CK(launch_jacobi_half(h->esum, h->js, g.N, h->st));
+  }
   double lam, mu;
   if (h->cref_mean) {
     int np = 0;
@@ -466,11 +488,12 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   double hh[3];
   for (int a = 0; a < g.d; ++a) hh[a] = 1.0 / g.n[a];
   h->ec_ref = make_elem_const(g.d, hh, lam, mu);
+  h->ec_ref.elem = h->element;
   s = build_symbol(h);
   if (s) return s;
   if (h->precision == JFFT_PREC_MIXED) {
     CK(launch_to_f32(h->E, h->E32, g.N, 1, nullptr, h->st));
-    CK(launch_to_f32(h->js, h->js32, g.N, 1, nullptr, h->st));
+    CK(launch_to_f32(h->js, h->js32, g.N * (h->element == JFFT_ELEM_P1 ? 2 : 1), 1, nullptr, h->st));
     CK(launch_to_f32(h->G, h->G32, g.F * h->ds, 1, nullptr, h->st));
     for (int a = 0; a < g.d; ++a)
       CK(launch_to_f32(reinterpret_cast<const double*>(h->tw[a]), reinterpret_cast<float*>(h->tw32[a]), 2 * g.n[a], 1,
@@ -525,6 +548,10 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   jfft_status s = validate_material(h, mat, g.N);
   if (s) return bail(s);
 
+  if (o.element != JFFT_ELEM_Q1 && o.element != JFFT_ELEM_P1) return bail(fail(h, JFFT_ERR_ARG, "unknown element"));
+  if (o.element == JFFT_ELEM_P1 && d != 2) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "P1 triangles are 2D"));
+  h->element = o.element;
+  h->jcs = h->element == JFFT_ELEM_P1 ? g.N : 0;
   // unit material and reference material
   set_unit_material(h, mat->nu);
   if (C_ref) {
@@ -566,7 +593,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   const int nbmax = h->max_loads;
   const int64_t spec_n = (int64_t)nbmax * d * g.F;
   const size_t part_rows = (size_t)nbmax * 6;
-  const size_t total = plan_bytes(g, h->ds, nbmax, o.precision);
+  const size_t total = plan_bytes(g, h->ds, nbmax, o.precision, h->element);
   if (o.hbm_budget && total > o.hbm_budget) {
     char msg[160];
     snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds hbm_budget %zu", total, o.hbm_budget);
@@ -581,7 +608,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->field, g.N * sizeof(double));
   AL(h->E, g.N * sizeof(double));
   AL(h->esum, g.N * sizeof(double));
-  AL(h->js, g.N * sizeof(double));
+  AL(h->js, g.N * sizeof(double) * (h->element == JFFT_ELEM_P1 ? 2 : 1));
   AL(h->G, (size_t)g.F * h->ds * sizeof(double));
   for (int a = 0; a < d; ++a) AL(h->tw[a], (size_t)g.n[a] * sizeof(double2));
   AL(h->T, (size_t)spec_n * sizeof(double2));
@@ -602,7 +629,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->active, nbmax * sizeof(int));
   if (o.precision == JFFT_PREC_MIXED) {
     AL(h->E32, g.N * sizeof(float));
-    AL(h->js32, g.N * sizeof(float));
+    AL(h->js32, g.N * sizeof(float) * (h->element == JFFT_ELEM_P1 ? 2 : 1));
     AL(h->G32, (size_t)g.F * h->ds * sizeof(float));
     for (int a = 0; a < d; ++a) AL(h->tw32[a], (size_t)g.n[a] * sizeof(float2));
     AL(h->T32, (size_t)spec_n * sizeof(float2));
@@ -717,17 +744,17 @@ static cudaError_t precond_op(jfft_solver* h, const Work<double>& w, int pc, con
                               CgState* cg, int* np, StageCtl sc = no_stage()) {
   if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
     return launch_green_precond(h->g, w.pl, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js,
-                                pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st, sc);
+                                pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st, sc, h->jcs);
   return launch_jacobi_precond(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
-                               h->partial, np, cg, h->st, sc);
+                               h->partial, np, cg, h->st, sc, h->jcs);
 }
 static cudaError_t precond_op(jfft_solver* h, const Work<float>& w, int pc, const float* r, float* z, int nb,
                               CgState* cg, int* np, StageCtl sc = no_stage()) {
   if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
     return launch_green_precond_f32(h->g, w.pl, r, z, nb, w.js, h->jscale, h->void_js, pc == JFFT_PC_GREEN_JACOBI,
-                                    h->partial, np, cg, h->st, sc);
+                                    h->partial, np, cg, h->st, sc, h->jcs);
   return launch_jacobi_precond_f32(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
-                                   h->partial, np, cg, h->st, sc);
+                                   h->partial, np, cg, h->st, sc, h->jcs);
 }
 
 static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, int nb, CgState* cg, int* np) {
@@ -1164,7 +1191,8 @@ extern "C" jfft_status jfft_get_diag(jfft_solver* h, int method, double* diag) {
   if (!diag) return fail(h, JFFT_ERR_ARG, "NULL output");
   const Grid& g = h->g;
   if (method == JFFT_DIAG_CLOSED_FORM) {
-    CK(launch_diag_closed(g, h->esum, h->kappa, h->z, h->st));
+    if (h->element == JFFT_ELEM_P1) CK(launch_diag_p1(g, h->E, h->kappa_p1, h->z, h->st));
+    else CK(launch_diag_closed(g, h->esum, h->kappa, h->z, h->st));
   } else if (method == JFFT_DIAG_COMBS) {
     for (int a = 0; a < g.d; ++a)
       for (int off = 0; off < (1 << g.d); ++off) {
@@ -1339,7 +1367,7 @@ extern "C" jfft_status jfft_workspace_estimate(const jfft_grid* grid, const jfft
   if (nbmax < g.d) nbmax = g.d;
   if (nbmax > kMaxLoads) return JFFT_ERR_ARG;
   if (o.precision != JFFT_PREC_FP64 && o.precision != JFFT_PREC_MIXED) return JFFT_ERR_ARG;
-  *bytes = plan_bytes(g, g.d * (g.d + 1) / 2, nbmax, o.precision);
+  *bytes = plan_bytes(g, g.d * (g.d + 1) / 2, nbmax, o.precision, o.element);
   return JFFT_OK;
 }
 

@@ -50,6 +50,7 @@ template <typename T> struct ElemConstT {
   T gs[3];       // (2 / h_a) / 2^d: mode -> displacement-gradient factor
   T lam, mu;     // Lame constants of the unit material
   T vol;         // element volume
+  int elem;      // voxel discretisation: 0 = Q1 (full Gauss rule), 1 = two P1 triangles (2D)
 };
 using ElemConst = ElemConstT<double>;
 
@@ -66,6 +67,7 @@ template <typename T> inline ElemConstT<T> elem_const_as(const ElemConst& e) {
   o.lam = (T)e.lam;
   o.mu = (T)e.mu;
   o.vol = (T)e.vol;
+  o.elem = e.elem;
   return o;
 }
 
@@ -166,6 +168,9 @@ cudaError_t launch_stress(const Grid& g, const ElemConst& ec, const double* E, c
 // S5: esum[I] = sum of E over the 2^d voxels at node I; js = esum^-1/2 (0 for 0).
 cudaError_t launch_node_esum(const Grid& g, const double* E, double* esum, cudaStream_t st);
 cudaError_t launch_jacobi_half(const double* esum, double* js, int64_t N, cudaStream_t st);
+// P1 voxels: diag[a][I] = sum over the 4 voxels around node I of E * kappa_o(a), o the
+// corner of that voxel at I (kappa4: [4 corners][2 components], corner c = o0 * 2 + o1).
+cudaError_t launch_diag_p1(const Grid& g, const double* E, const double* kappa4, double* diag, cudaStream_t st);
 // diag[a][I] = kappa[a] * esum[I]
 cudaError_t launch_diag_closed(const Grid& g, const double* esum, const double* kappa3, double* diag, cudaStream_t st);
 // Alg. 2 helpers: comb field of one component / offset pattern, and extraction.
@@ -192,19 +197,19 @@ using FftPlan = FftPlanT<double>;
 cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
                                  int64_t field_stride, const double* js, const double* jscale, double void_js,
                                  bool jacobi, double* partial, int* nparts, CgState* cg, cudaStream_t st,
-                                 StageCtl sc = no_stage());
+                                 StageCtl sc = no_stage(), int64_t jcs = 0);
 // The same in FP32 (mixed-precision inner solve).
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
                                      const float* js, const double* jscale, double void_js, bool jacobi,
                                      double* partial, int* nparts, CgState* cg, cudaStream_t st,
-                                     StageCtl sc = no_stage());
+                                     StageCtl sc = no_stage(), int64_t jcs = 0);
 // Forward transform of nb d-component real fields -> line-major spectrum [nb][d][F].
 cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
                                     const double2** spec_out, cudaStream_t st);
 // z = J r (J = diag(K)^-1 with the void rule) or z = r (identity), partial r.z.
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
                                   const double* jscale, double void_js, bool identity, double* partial, int* nparts,
-                                  CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
+                                  CgState* cg, cudaStream_t st, StageCtl sc = no_stage(), int64_t jcs = 0);
 
 // S4: CG vector updates and inner products (T = double or float; scalars in FP64).
 template <typename T>
@@ -218,7 +223,8 @@ cudaError_t launch_dot(const Grid& g, const T* a, const T* c, int nb, int64_t st
 // FP32 variant of the Jacobi / identity preconditioner.
 cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
                                       const double* jscale, double void_js, bool identity, double* partial,
-                                      int* nparts, CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
+                                      int* nparts, CgState* cg, cudaStream_t st, StageCtl sc = no_stage(),
+                                      int64_t jcs = 0);
 // Precision conversions for the refinement loop: dst = (float) src per rhs, zeroed
 // where active[b] == 0; u += (double) d; r = f - q with partial sums of r.r.
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n_per_rhs, int nb, const int* active, cudaStream_t st);

@@ -223,7 +223,8 @@ constexpr int kWarpsPerCta2d = 4;
 
 // HAS_X = false: x = 0 (right-hand side); SHIFT: the load's macroscopic strain is added
 // to the element modes; the output is sgn * (K x + K_shift).
-template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT>
+// P1: the voxel is two linear triangles (tri_pair_force) instead of the Q1 element.
+template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, bool P1>
 __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
     k_apply_K2d(Grid g, ElemConstT<T> ec, const T* __restrict__ E, T e_uniform, const T* __restrict__ x,
                 T* __restrict__ y, int64_t fstride, int seg, int groups, const StrainShift* __restrict__ shifts,
@@ -291,7 +292,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
         u[a][2] = hi[a];   // corner (1, 0): node (e0 + 1, c)
         u[a][3] = rhi[a];  // corner (1, 1): node (e0 + 1, c + 1)
       }
-      element_force<2, T, SHIFT>(ec, &sh, u, Ee);
+      if (P1) tri_pair_force<T, SHIFT>(ec, &sh, u, Ee);
+      else element_force<2, T, SHIFT>(ec, &sh, u, Ee);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const T from_left_lo = __shfl_up_sync(0xffffffffu, u[a][1], 1);
@@ -327,8 +329,12 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* 
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
                      : DOT == 1 ? "apply_K"
                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
-  JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
-                       g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
+  if (ec.elem == 1)
+    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+                         g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
+  else
+    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+                         g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
@@ -538,6 +544,7 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
       if (hx && dot_mode == 0) return apply_K2d_t<double, 0, true, true, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial, nparts, cg, st, sc, shifts, sgn);
     }
   }
+  if (ec.elem != 0) return cudaErrorInvalidValue;  // P1 voxels run only on the 2D warp kernel
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
     return apply_K_t<double, D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st, sc);
@@ -649,7 +656,12 @@ __global__ void __launch_bounds__(256) k_stress(Grid g, ElemConst ec, const doub
       for (int a = 0; a < D; ++a) uc[a][c] = ub[a * g.N + node];
     }
     double sig[6];
-    element_stress<D>(ec, &sh, uc, E[e], sig);
+    if constexpr (D == 2) {
+      if (ec.elem == 1) tri_pair_stress(ec, &sh, uc, E[e], sig);
+      else element_stress<D>(ec, &sh, uc, E[e], sig);
+    } else {
+      element_stress<D>(ec, &sh, uc, E[e], sig);
+    }
 #pragma unroll
     for (int s = 0; s < DS; ++s) {
       if (stress) stress[((int64_t)b * DS + s) * g.N + e] = sig[s];
@@ -710,6 +722,36 @@ __global__ void k_jacobi_half(const double* __restrict__ esum, double* __restric
 cudaError_t launch_jacobi_half(const double* esum, double* js, int64_t N, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
   JFFT_K("jacobi_half", st, k_jacobi_half<<<blocks, 256, 0, st>>>(esum, js, N));
+  return cudaGetLastError();
+}
+
+struct Kappa8 { double k[4][2]; };
+
+// P1 closed-form diagonal: node I is corner o of the voxel I - o; diag[a][I] =
+// sum_o E[I - o] kappa_o(a) (2D).
+__global__ void k_diag_p1(Grid g, const double* __restrict__ E, Kappa8 kap, double* __restrict__ diag) {
+  const int n0 = g.n[0], n1 = g.n[1];
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < g.N; I += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(I / n1), i1 = (int)(I % n1);
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int o0 = c >> 1, o1 = c & 1;
+      const double e = E[(int64_t)((i0 - o0 + n0) % n0) * n1 + (i1 - o1 + n1) % n1];
+      s0 += e * kap.k[c][0];
+      s1 += e * kap.k[c][1];
+    }
+    diag[I] = s0;
+    diag[g.N + I] = s1;
+  }
+}
+
+cudaError_t launch_diag_p1(const Grid& g, const double* E, const double* kappa4, double* diag, cudaStream_t st) {
+  Kappa8 k;
+  for (int c = 0; c < 4; ++c)
+    for (int a = 0; a < 2; ++a) k.k[c][a] = kappa4[c * 2 + a];
+  const int blocks = (int)std::min<int64_t>((g.N + 255) / 256, 152 * 16);
+  JFFT_K("diag_p1", st, k_diag_p1<<<blocks, 256, 0, st>>>(g, E, k, diag));
   return cudaGetLastError();
 }
 
