@@ -358,7 +358,7 @@ def main():
         then the timed steps with per-kernel CUDA events and clock sampling."""
         s = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
                    stream=stream.cuda_stream, io="device", max_loads=N_LOADS, precision=precision,
-                   graphs=not args.no_graphs)
+                   graphs=not args.no_graphs, autotune=True)
 
         def step(record=None):
             for c in CONTRASTS:
@@ -398,6 +398,7 @@ def main():
             times.append(e0.elapsed_time(e1))
         launches = s.launch_count - n0
         replays = s.graph_replays - r0
+        tuning = s.tuning
         clk = clocks.stop()
         # Per-kernel durations: one more step with a CUDA event pair around every kernel
         # launch (the PCG chunk then runs as a replayed graph with event nodes instead of
@@ -418,7 +419,7 @@ def main():
         s.close()
         ms, value = aggregate(statistics.mean(times), world, solves_per_step, dist, "cuda")
         return {"ms": ms, "value": value, "times": times, "rec": rec, "prof": prof, "launches": launches,
-                "graph_replays": replays, "profiled_step_ms": prof_times,
+                "graph_replays": replays, "profiled_step_ms": prof_times, "tuning": tuning,
                 "clocks": clk}
 
     def roofline(leg, alu):
@@ -620,6 +621,7 @@ def main():
         "rel_res_max": max(max(v["rel_res"]) for v in mixed["rec"].values()),
         "kernels_ms_total": {k: round(v[1], 3) for k, v in mixed["prof"].items()},
         "graph_replays": mixed["graph_replays"],
+        "tuning": mixed["tuning"],
         "profiled_step_ms": mixed["profiled_step_ms"],
     }
     clk = fp64["clocks"]
@@ -642,7 +644,8 @@ def main():
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "contrasts": list(CONTRASTS),
                        "preconditioners": list(PRECONDS), "loads": N_LOADS, "tol": TOL,
                        "parallelism": f"replicas x{world}",
-                       "l2": "256 MiB buffer written before each timed step (outside the timed interval)"},
+                       "l2": "256 MiB buffer written before each timed step (outside the timed interval)",
+                       "launch_shapes": "plan-time autotuner (options.autotune)"},
             "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": launches // args.steps,
             "clocks": clk, "mixed": mixed_line, "small_cells": cells_line, "serving": serving_line,
             "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
@@ -651,6 +654,7 @@ def main():
                        "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()},
                        "kernel_launches": {k: v[0] for k, v in prof.items()},
                        "graph_replays": fp64["graph_replays"],
+                       "tuning": fp64["tuning"],
                        "profiled_step_ms": fp64["profiled_step_ms"],
                        "step_ms": times},
         }

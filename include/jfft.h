@@ -127,6 +127,11 @@ typedef struct {
   int element;               /* voxel discretisation: JFFT_ELEM_Q1 (default, bilinear / trilinear, full
                                 Gauss rule) or JFFT_ELEM_P1 (2D only: each voxel split along its
                                 (0,0)-(1,1) diagonal into two linear triangles, Sec. 4) */
+  int autotune;              /* 1: at creation, time the candidate launch shapes of the operator and
+                                FFT passes (working precision, max_loads right-hand sides) and keep
+                                the fastest (jfft_get_tuning). 0 (default): built-in shapes. Shapes
+                                change only the block split: results differ at most by the rounding
+                                of the partial-sum reductions. */
 } jfft_options;
 
 typedef struct {
@@ -377,6 +382,14 @@ int64_t jfft_launch_count(const jfft_solver* h);
 
 /* Number of PCG chunks this handle has run as a CUDA graph replay (options.graphs). */
 int64_t jfft_graph_replays(const jfft_solver* h);
+
+/* Launch shapes in use, tune[4] (0 = built-in default): node rows per warp segment of
+ * the 2D operator {8, 16, 32, 64}; planes per segment of the 3D FP32 operator {4, 8, 16};
+ * divisor of the lines per block of the forward row / inverse column FFT pass {1, 2, 4}.
+ * jfft_set_tuning applies a saved choice (for example one found with options.autotune)
+ * and drops captured graphs; JFFT_ERR_ARG for values outside those sets. */
+jfft_status jfft_get_tuning(const jfft_solver* h, int* tune);
+jfft_status jfft_set_tuning(jfft_solver* h, const int* tune);
 
 /* When on, every kernel launch is bracketed by CUDA events on the handle's stream
  * and accumulated per kernel name; jfft_profile_json returns

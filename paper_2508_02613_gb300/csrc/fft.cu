@@ -338,7 +338,7 @@ static cudaError_t pass_rows_real_fwd(const Grid& g, const FftPlanT<T>& p, const
   const int Lin = g.n[g.d - 1];
   const int R = (int)(g.N / Lin);
   const int L = Lin / 2;
-  const int w = rows_per_cta<T>(L, R, Lin);
+  const int w = std::max(1, rows_per_cta<T>(L, R, Lin) / std::max(1, g.tune[2]));
   const size_t smem = rows_smem<T>(L, w, Lin);
   dim3 grid(R / w, nb * g.d);
   const int tpl = lanes_per_line<T>(L);
@@ -414,7 +414,7 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
   const int n = g.n[g.d - 1];
   const int R = (int)(g.N / n);
   const int L = n / 2;
-  const int w = rows_per_cta<T>(L, R, n);
+  const int w = std::max(1, rows_per_cta<T>(L, R, n) / std::max(1, g.tune[3]));
   const size_t smem = rows_smem<T>(L, w, n);
   dim3 grid(R / w, nb * g.d);
   const int tpl = lanes_per_line<T>(L);

@@ -255,6 +255,7 @@ extern "C" void jfft_default_options(jfft_options* o) {
   o->max_refine = 30;
   o->graphs = 1;
   o->element = JFFT_ELEM_Q1;
+  o->autotune = 0;
 }
 
 static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
@@ -502,6 +503,8 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   return sync(h);
 }
 
+static jfft_status autotune(jfft_solver* h);
+
 extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, const jfft_material* mat,
                                    const double* C_ref, const jfft_options* opt) {
   if (!out) return JFFT_ERR_ARG;
@@ -656,6 +659,10 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   }
   s = setup_material(h, mat, false);
   if (s) return bail(s);
+  if (o.autotune) {
+    s = autotune(h);
+    if (s) return bail(s);
+  }
   g_cur = nullptr;
   *out = h;
   return JFFT_OK;
@@ -755,6 +762,60 @@ static cudaError_t precond_op(jfft_solver* h, const Work<float>& w, int pc, cons
                                     h->partial, np, cg, h->st, sc, h->jcs);
   return launch_jacobi_precond_f32(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
                                    h->partial, np, cg, h->st, sc, h->jcs);
+}
+
+// Plan-time autotuner: times the candidate launch shapes of the working precision's
+// operator and FFT passes on this grid and batch size (a few launches each, after one
+// warm-up, CUDA events on the solver's stream) and keeps the fastest in g.tune. The
+// shapes change only how the work is split into blocks, so results differ from the
+// defaults at most by the rounding of the partial-sum reductions.
+template <typename T>
+static jfft_status autotune_t(jfft_solver* h, const Work<T>& w) {
+  const Grid& g = h->g;
+  const int nb = h->max_loads;
+  const int64_t fe = field_elems(h);
+  CK(cudaMemsetAsync(w.p, 0, nb * fe * sizeof(T), h->st));
+  CK(cudaMemsetAsync(w.r, 0, nb * fe * sizeof(T), h->st));
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  int np = 0;
+  auto time = [&](auto&& launch) -> float {
+    if (launch() != cudaSuccess) return 1e30f;
+    cudaEventRecord(a, h->st);
+    for (int i = 0; i < 5; ++i)
+      if (launch() != cudaSuccess) return 1e30f;
+    cudaEventRecord(b, h->st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  };
+  auto pick = [&](int slot, std::initializer_list<int> cands, auto&& launch) {
+    float best = 1e30f;
+    int arg = 0;
+    for (int c : cands) {
+      h->g.tune[slot] = c;
+      const float t = time(launch);
+      if (t < best) { best = t; arg = c; }
+    }
+    h->g.tune[slot] = arg;
+  };
+  auto op = [&]() { return apply_op(h, w, w.p, w.q, nb, 1, &np, nullptr); };
+  auto pre = [&]() { return precond_op(h, w, JFFT_PC_GREEN_JACOBI, w.r, w.z, nb, nullptr, &np); };
+  if (g.d == 2) pick(0, {8, 16, 32, 64}, op);
+  else if (sizeof(T) == 4) pick(1, {4, 8, 16}, op);
+  pick(2, {1, 2, 4}, pre);
+  pick(3, {1, 2, 4}, pre);
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return sync(h);
+}
+
+static jfft_status autotune(jfft_solver* h) {
+  if (h->precision == JFFT_PREC_MIXED) return autotune_t<float>(h, work32(h));
+  return autotune_t<double>(h, work64(h));
 }
 
 static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, int nb, CgState* cg, int* np) {
@@ -1322,6 +1383,34 @@ extern "C" jfft_status jfft_postprocess(jfft_solver* h, int count, const double*
 // ------------------------------------------------------------- instrumentation
 extern "C" int64_t jfft_launch_count(const jfft_solver* h) { return h ? h->launches : 0; }
 extern "C" int64_t jfft_graph_replays(const jfft_solver* h) { return h ? h->graph_replays : 0; }
+
+extern "C" jfft_status jfft_get_tuning(const jfft_solver* h, int* tune) {
+  if (!h || !tune) return JFFT_ERR_ARG;
+  for (int i = 0; i < 4; ++i) tune[i] = h->g.tune[i];
+  return JFFT_OK;
+}
+
+extern "C" jfft_status jfft_set_tuning(jfft_solver* h, const int* tune) {
+  if (!h || !tune) return JFFT_ERR_ARG;
+  static const int allowed[4][5] = {{0, 8, 16, 32, 64}, {0, 4, 8, 16, 0}, {0, 1, 2, 4, 0}, {0, 1, 2, 4, 0}};
+  for (int i = 0; i < 4; ++i) {
+    bool ok = false;
+    for (int j = 0; j < 5; ++j) ok = ok || (tune[i] == allowed[i][j] && (j == 0 || allowed[i][j] != 0));
+    if (!ok) return fail(h, JFFT_ERR_ARG, "tuning value outside the candidate set");
+  }
+  CurGuard guard(h);
+  jfft_status s = sync(h);
+  if (s) return s;
+  for (int i = 0; i < 4; ++i) h->g.tune[i] = tune[i];
+  // captured graphs hold the old launch shapes
+  for (auto& gr : h->graph) drop_graph(h, gr);
+  for (auto& lg : h->loop)
+    if (lg.exec) {
+      cudaGraphExecDestroy(lg.exec);
+      lg.exec = nullptr;
+    }
+  return JFFT_OK;
+}
 
 extern "C" jfft_status jfft_set_profiling(jfft_solver* h, int on) {
   if (!h) return JFFT_ERR_ARG;

@@ -27,6 +27,11 @@ struct Grid {
   int64_t N;        // product of n
   int M;            // n[d-1] / 2, half length of the real axis
   int64_t F;        // number of half-spectrum frequencies: N / n[d-1] * (M + 1)
+  // Launch-shape choices (0 = the built-in default; set by the plan-time autotuner):
+  // [0] node rows per warp segment of the 2D operator, [1] planes per segment of the 3D
+  // FP32 operator, [2] / [3] divisor of the lines per block of the forward row pass /
+  // inverse column pass of the FFT.
+  int tune[4];
 };
 
 // Element constants of the Q1 operator in Walsh-Hadamard mode form.

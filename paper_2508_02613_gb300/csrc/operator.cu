@@ -323,7 +323,7 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* 
                                StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
   const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
   const int ctas_x = (groups + kWarpsPerCta2d - 1) / kWarpsPerCta2d;
-  int seg = std::min(g.n[0], 16);
+  int seg = std::min(g.n[0], g.tune[0] > 0 ? g.tune[0] : 16);
   while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
   dim3 grid(ctas_x, g.n[0] / seg, nb);
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
@@ -476,7 +476,7 @@ static cudaError_t apply_K3d_t(const Grid& g, const ElemConstT<T>& ec, const T* 
   const int rowblocks = g.n[1] / J;
   const int warps = groups2 * rowblocks;
   const int ctas_x = (warps + kWarpsPerCta3d - 1) / kWarpsPerCta3d;
-  int seg = std::min(g.n[0], JFFT_K3D_SEG);
+  int seg = std::min(g.n[0], g.tune[1] > 0 ? g.tune[1] : JFFT_K3D_SEG);
   while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
   dim3 grid(ctas_x, g.n[0] / seg, nb);
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")

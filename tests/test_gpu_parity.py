@@ -339,6 +339,27 @@ def test_graph_replay_matches_direct_launches(precision):
         assert np.array_equal(o["u"], outs[0]["u"]) and np.array_equal(o["C_hom"], outs[0]["C_hom"])
 
 
+@pytest.mark.parametrize("shape,precision", [((256, 128), "fp64"), ((256, 128), "mixed"), ((32, 32, 64), "mixed")])
+def test_autotuned_launch_shapes(shape, precision):
+    """options.autotune picks shapes from the candidate sets; the tuned solve meets the
+    tolerance (true residual) and agrees with the default-shape solve within 10 tol (the
+    shapes change only the rounding of the partial-sum reductions, which can move the
+    iteration count); set_tuning reproduces the tuned run bit for bit."""
+    d = len(shape)
+    rho, _ = _problem(shape, 15)
+    tuned = _solver(shape, rho, precision=precision, autotune=True)
+    t = tuned.tuning
+    assert t[0] in (0, 8, 16, 32, 64) and t[1] in (0, 4, 8, 16) and t[2] in (0, 1, 2, 4) and t[3] in (0, 1, 2, 4)
+    a = tuned.solve(mandel_unit_loads(d), 1e-8, "green_jacobi")
+    base = _solver(shape, rho, precision=precision).solve(mandel_unit_loads(d), 1e-8, "green_jacobi")
+    assert a["rel_res"].max() <= 1e-8 * 1.01
+    assert np.linalg.norm(a["u"] - base["u"]) <= 10 * 1e-8 * np.linalg.norm(base["u"])
+    again = _solver(shape, rho, precision=precision)
+    again.set_tuning(t)
+    b = again.solve(mandel_unit_loads(d), 1e-8, "green_jacobi")
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["iters"], b["iters"])
+
+
 def test_device_io_matches_host_io():
     torch = pytest.importorskip("torch")
     shape = (32, 64)
