@@ -53,6 +53,33 @@ template <int D, typename V> JFFT_HD void wht_bwd(V* v) {
   }
 }
 
+// wht_bwd for a vector whose entry 0 is zero (v[0] is not read).
+template <int D, typename V> JFFT_HD void wht_bwd_z0(V* v) {
+  {
+    const V y1 = v[1];
+    v[0] = -y1;
+    v[1] = y1;
+#pragma unroll
+    for (int c = 2; c < (1 << D); c += 2) {
+      const V y0 = v[c], z1 = v[c | 1];
+      v[c] = y0 - z1;
+      v[c | 1] = y0 + z1;
+    }
+  }
+#pragma unroll
+  for (int a = 1; a < D; ++a) {
+    const int s = 1 << a;
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+      if (!(c & s)) {
+        V y0 = v[c], y1 = v[c | s];
+        v[c] = y0 - y1;
+        v[c | s] = y0 + y1;
+      }
+    }
+  }
+}
+
 template <int D> JFFT_HD constexpr int popc(int m) {
   return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1);
 }
@@ -113,11 +140,13 @@ JFFT_HD void element_force(const ElemConstT<V>& ec, const StrainShift* sh, V (*u
       for (int b = 0; b < D; ++b) u[a][mbit<D>(b)] += V(sh->s[a][b]);
   }
   mode_forces<D>(ec, u, F);
+  // Mode 0 (rigid translation) carries no force: it is left out of the scaling and
+  // of the first butterfly stage instead of being multiplied and added as a zero.
 #pragma unroll
   for (int a = 0; a < D; ++a) {
 #pragma unroll
-    for (int m = 0; m < NC; ++m) u[a][m] = F[a][m] * E;
-    wht_bwd<D>(u[a]);
+    for (int m = 1; m < NC; ++m) u[a][m] = F[a][m] * E;
+    wht_bwd_z0<D>(u[a]);
   }
 }
 

@@ -60,6 +60,8 @@ template <typename T, bool INV> struct Dft<T, 4, INV> {
 
 // Radix-2 split of a size-2H DFT into two size-H DFTs (even / odd samples):
 // X[k] = E[k] + W^k O[k], X[k + H] = E[k] - W^k O[k], W = exp(-+ 2 pi i / 2H).
+// W^0 = 1 and W^(H/2) = -+i are applied without multiplications (same values up to
+// the sign of zero results).
 template <typename T, int H, bool INV> __device__ __forceinline__ void split2(cplx<T>* v, const cplx<T>* w) {
   cplx<T> e[H], o[H];
 #pragma unroll
@@ -71,7 +73,7 @@ template <typename T, int H, bool INV> __device__ __forceinline__ void split2(cp
   Dft<T, H, INV>::run(o);
 #pragma unroll
   for (int k = 0; k < H; ++k) {
-    const cplx<T> t = c_mul<T>(o[k], w[k]);
+    const cplx<T> t = k == 0 ? o[k] : (2 * k == H ? c_mi<T, INV>(o[k]) : c_mul<T>(o[k], w[k]));
     v[k] = c_add<T>(e[k], t);
     v[k + H] = c_sub<T>(e[k], t);
   }

@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
         const T from_left_lo = __shfl_up_sync(0xffffffffu, u[a][1], 1);
         const T from_left_hi = __shfl_up_sync(0xffffffffu, u[a][3], 1);
         if (e0 >= L0 && writer) {
-          const T q = sgn * (carry[a] + u[a][0] + from_left_lo);
+          const T sum = carry[a] + u[a][0] + from_left_lo;
+          const T q = SHIFT ? sgn * sum : sum;  // sgn is 1 for the forms without a strain shift
           yb[a * g.N + (int64_t)e0 * n1 + ocol] = q;
           if (DOT == 1) dot += lo[a] * q;
           if (DOT == 2) dot += q * q;
@@ -447,7 +448,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta3d, JFFT_K3D_MINB)
           const T t11 = u[a][6] + __shfl_up_sync(0xffffffffu, u[a][7], 1);
           if (out_row) {
             if (e0 >= L0 && writer) {
-              const T q = sgn * (carry[k - 1][a] + pacc[a] + t00);
+              const T sum = carry[k - 1][a] + pacc[a] + t00;
+              const T q = SHIFT ? sgn * sum : sum;  // sgn is 1 for the forms without a strain shift
               yb[a * N + (b0 + (e1 & (n1 - 1))) * n2 + (o & (n2 - 1))] = q;
               if (DOT == 1) dot += lo0[a] * q;
               if (DOT == 2) dot += q * q;

@@ -47,7 +47,13 @@ def test_cells_converged_match_oracle(shape, pc):
         nrm = np.linalg.norm(ref.u)
         assert np.linalg.norm(out["u"][k] - ref.u) <= 1e-10 * nrm, k
         assert rel(out["C_hom"][k], ref.C_hom) <= 1e-9, k
-        assert np.all(np.abs(out["iters"][k] - ref.iters) <= 1), (out["iters"][k], ref.iters)
+        # iteration count: within one of the oracle's range over two summation orders (the
+        # Green runs take up to ~550 iterations and creep along 1e-12, where rounding alone
+        # moves the stopping iteration by two)
+        seq = osolve.solve(prob, eps, 1e-12, pc, dot_order="sequential")
+        lo = np.minimum(ref.iters, seq.iters) - 1
+        hi = np.maximum(ref.iters, seq.iters) + 1
+        assert np.all((lo <= out["iters"][k]) & (out["iters"][k] <= hi)), (out["iters"][k], ref.iters, seq.iters)
         assert out["rel_res"][k].max() <= 1e-11
 
 
