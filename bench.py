@@ -171,6 +171,13 @@ def traffic_bytes_per_unit(kernel, shape, d=2):
     return table.get(k)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch with all three
+# loads active, from the ncu capture summarised in profiles/fp64_2d_1024_gj_kernels.md
+# (1024 x 1024, Green-Jacobi, contrast 1e4). Valid for the kernels of that capture; the
+# FP32 kernels have no current capture (their traffic stays null).
+NCU_TRAFFIC_PER_LAUNCH = {"apply_K": 59.59e6 + 9.87e6, "fft_lines": 63.12e6 + 1.11e6}
+
+
 def aggregate(ms_local, world, solves_per_step, dist=None, device=None):
     """Whole-job throughput of N independent replicas: every rank ran the same
     per-rank workload; the job time is the slowest rank's time (max over ranks, the
@@ -437,6 +444,10 @@ def main():
                 continue
             out = {"kernel": name, "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
                    "traffic": None, "algorithmic_bytes_per_unit": byt, "units": n_units}
+            if name in NCU_TRAFFIC_PER_LAUNCH:
+                out["traffic"] = NCU_TRAFFIC_PER_LAUNCH[name]
+                out["traffic_note"] = ("DRAM bytes of one 3-load launch (ncu); the algorithmic bytes of that "
+                                       f"launch are {3 * byt:.4g} (L2 keeps part of the fields)")
             gbs = n_units * byt / (tot / 1e3) / 1e9
             tfl = n_units * fl / (tot / 1e3) / 1e12
             if alu:

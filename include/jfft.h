@@ -132,6 +132,12 @@ typedef struct {
                                 the fastest (jfft_get_tuning). 0 (default): built-in shapes. Shapes
                                 change only the block split: results differ at most by the rounding
                                 of the partial-sum reductions. */
+  int reliable;              /* MIXED: 0 (default): every refinement step restarts CG on the new
+                                residual (classic iterative refinement). 1: reliable updates: the
+                                FP64 residual f - K u replaces the FP32 recurrence residual and,
+                                for each load whose recurrence residual is within 10 % of it, the
+                                search direction is kept (beta from the last r.z) instead of
+                                restarting. */
 } jfft_options;
 
 typedef struct {

@@ -86,7 +86,8 @@ template cudaError_t launch_cg_xr<double>(const Grid&, double*, double*, const d
 template cudaError_t launch_cg_xr<float>(const Grid&, float*, float*, const float*, const float*, int, int64_t,
                                          CgState*, double*, int*, cudaStream_t, StageCtl);
 
-// p = z + beta p
+// p = z + beta p (p = z where beta = 0, so that a p left over from an earlier run is
+// never read then)
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_p(typename V16<T>::t* __restrict__ p, const typename V16<T>::t* __restrict__ z,
                                               int64_t n16, int64_t stride16, const CgState* __restrict__ cg) {
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256) k_cg_p(typename V16<T>::t* __restrict__ p
       T* pa = reinterpret_cast<T*>(&pv[u]);
       const T* za = reinterpret_cast<const T*>(&zv[u]);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) pa[c] = fma(be, pa[c], za[c]);
+      for (int c = 0; c < NV; ++c) pa[c] = be == T(0) ? za[c] : fma(be, pa[c], za[c]);
     }
     p[off + i] = pv[0];
     if (two) p[off + i2] = pv[1];
@@ -126,11 +127,10 @@ cudaError_t launch_cg_p(const Grid& g, T* p, const T* z, int nb, int64_t stride,
 template cudaError_t launch_cg_p<double>(const Grid&, double*, const double*, int, int64_t, CgState*, cudaStream_t);
 template cudaError_t launch_cg_p<float>(const Grid&, float*, const float*, int, int64_t, CgState*, cudaStream_t);
 
-// z = J r (J = (J^1/2)^2 per component; identity: z = r), partial r.z
+// z = J r (J = (J^1/2)^2 per DOF from the resolved table; identity: z = r), partial r.z
 template <typename T>
 __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__ r, T* __restrict__ z, int64_t stride,
-                                                   const T* __restrict__ js, double3 jscale, double void_js,
-                                                   int identity, CgState* __restrict__ cg,
+                                                   const T* __restrict__ js, int identity, CgState* __restrict__ cg,
                                                    double* __restrict__ partial, StageCtl sc, int64_t jcs) {
   const int b = blockIdx.y;
   if (cg && cg[b].done) return;
@@ -142,9 +142,7 @@ __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__
     T zv = rv;
     if (!identity) {
       const int a = (int)(i / g.N);
-      const T s = js[i - a * g.N + a * jcs];
-      const T ka = (T)(a == 0 ? jscale.x : (a == 1 ? jscale.y : jscale.z));
-      const T jh = s > T(0) ? s * ka : (T)void_js;
+      const T jh = js[i - a * g.N + a * jcs];
       zv = jh * jh * rv;
     }
     z[off + i] = zv;
@@ -156,25 +154,23 @@ __global__ void __launch_bounds__(256) k_jacobi_pc(Grid g, const T* __restrict__
 }
 
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
-                                  const double* jscale, double void_js, bool identity, double* partial, int* nparts,
-                                  CgState* done, cudaStream_t st, StageCtl sc, int64_t jcs) {
+                                  bool identity, double* partial, int* nparts, CgState* done, cudaStream_t st,
+                                  StageCtl sc, int64_t jcs) {
   const int bl = vec_blocks(g.d * g.N / 2);
   JFFT_K("jacobi_pc", st,
-         k_jacobi_pc<double><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
-                                                           make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                                           identity ? 1 : 0, done, partial, sc, jcs));
+         k_jacobi_pc<double><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js, identity ? 1 : 0, done, partial, sc,
+                                                           jcs));
   *nparts = bl;
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
-                                      const double* jscale, double void_js, bool identity, double* partial,
-                                      int* nparts, CgState* done, cudaStream_t st, StageCtl sc, int64_t jcs) {
+                                      bool identity, double* partial, int* nparts, CgState* done, cudaStream_t st,
+                                      StageCtl sc, int64_t jcs) {
   const int bl = vec_blocks(g.d * g.N / 2);
   JFFT_K("jacobi_pc_f32", st,
-         k_jacobi_pc<float><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js,
-                                                          make_double3(jscale[0], jscale[1], jscale[2]), void_js,
-                                                          identity ? 1 : 0, done, partial, sc, jcs));
+         k_jacobi_pc<float><<<dim3(bl, nb), 256, 0, st>>>(g, r, z, stride, js, identity ? 1 : 0, done, partial, sc,
+                                                          jcs));
   *nparts = bl;
   return cudaGetLastError();
 }
@@ -227,18 +223,45 @@ cudaError_t launch_cg_continue(const CgState* cg, int nb, int* chunks, int cap, 
 
 // Scalar stages as a separate launch; one block per rhs (the same reduction order
 // and update as the fused tails of the producing kernels).
+// keep (kStageInitFFKeep only, may be NULL): right-hand sides with keep[b] != 2 start
+// afresh (kStageInitFF).
 __global__ void __launch_bounds__(256) k_scalars(int stage, CgState* __restrict__ cg, const double* __restrict__ partial,
-                                                 int nparts, double tol, int stop_mode, int max_iter) {
+                                                 int nparts, double tol, int stop_mode, int max_iter,
+                                                 const int* __restrict__ keep) {
   const int b = blockIdx.x;
   CgState& s = cg[b];
-  if (stage != kStageInitFF && s.done) return;
+  if (stage == kStageInitFFKeep && keep && keep[b] != 2) stage = kStageInitFF;
+  if (stage != kStageInitFF && stage != kStageInitFFKeep && s.done) return;
   const double v = canonical_sum(partial + (int64_t)b * kMaxPartials, nparts);
   if (threadIdx.x == 0) apply_stage(s, stage, v, tol, stop_mode, max_iter);
 }
 
 cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,
-                              int stop_mode, int max_iter, cudaStream_t st) {
-  JFFT_K("cg_scalars", st, k_scalars<<<nb, 256, 0, st>>>(stage, cg, partial, nparts, tol, stop_mode, max_iter));
+                              int stop_mode, int max_iter, cudaStream_t st, const int* keep) {
+  JFFT_K("cg_scalars", st, k_scalars<<<nb, 256, 0, st>>>(stage, cg, partial, nparts, tol, stop_mode, max_iter, keep));
+  return cudaGetLastError();
+}
+
+// partial[b][blk] = sum (r64 - r32)^2 over right-hand side b: the distance between the
+// FP64 residual and the FP32 recurrence residual it replaces.
+__global__ void __launch_bounds__(256) k_gap(const double* __restrict__ r64, const float* __restrict__ r32, int64_t n,
+                                             double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  const int64_t off = (int64_t)b * n;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double e = r64[off + i] - (double)r32[off + i];
+    acc = fma(e, e, acc);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x] = s;
+}
+
+cudaError_t launch_gap(const Grid& g, const double* r64, const float* r32, int nb, double* partial, int* nparts,
+                       cudaStream_t st) {
+  const int bl = vec_blocks(g.d * g.N / 2);
+  JFFT_K("gap", st, k_gap<<<dim3(bl, nb), 256, 0, st>>>(r64, r32, g.d * g.N, partial));
+  *nparts = bl;
   return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ struct jfft_solver {
   double e_ref = 1.0;
   double kappa[3] = {0, 0, 0}, jscale[3] = {0, 0, 0}, void_js = 1.0;
   int element = 0;                 // JFFT_ELEM_Q1 or JFFT_ELEM_P1
-  int64_t jcs = 0;                 // component stride of the J^1/2 node factors (P1: N)
+  int64_t jcs = 0;                 // component stride of the resolved J^1/2 table (0: one factor per node)
   double kappa_p1[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // P1: diagonal of the unit voxel, [corner][component]
   double scale_store = 1.0;
   // device workspace
@@ -256,6 +256,7 @@ extern "C" void jfft_default_options(jfft_options* o) {
   o->graphs = 1;
   o->element = JFFT_ELEM_Q1;
   o->autotune = 0;
+  o->reliable = 0;
 }
 
 static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
@@ -329,13 +330,24 @@ static jfft_status build_symbol(jfft_solver* h) {
   return JFFT_OK;
 }
 
+// Components of the resolved J^1/2 table: one factor per node when every component
+// scales alike (Q1 on a grid with equal spacing on every axis), one per DOF otherwise
+// (P1 voxels, or Q1 elements that are not cubes).
+static int js_components(const Grid& g, int element) {
+  if (element == JFFT_ELEM_P1) return g.d;
+  for (int a = 1; a < g.d; ++a)
+    if (g.n[a] != g.n[0]) return g.d;
+  return 1;
+}
+
 // Device workspace of a solver (bytes), as allocated by jfft_create.
 static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int element = 0) {
   const int d = g.d;
   const int64_t fe = (int64_t)d * g.N;
   const int64_t spec_n = (int64_t)nbmax * d * g.F;
   size_t total = 0;
-  total += (4 + (element == 1 ? 1 : 0)) * g.N * sizeof(double);   // field, E, esum, js (per DOF for P1)
+  const int jsn = js_components(g, element);
+  total += (3 + jsn) * g.N * sizeof(double);                        // field, E, esum, J^1/2 table
   total += (size_t)g.F * ds * sizeof(double);                       // G
   for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(double2);
   total += (size_t)spec_n * sizeof(double2) * (d == 3 ? 2 : 1);     // T (U)
@@ -344,7 +356,7 @@ static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int el
   total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int) + sizeof(unsigned));
   total += sizeof(int);                                             // chunk counter
   if (precision == JFFT_PREC_MIXED) {
-    total += (2 + (element == 1 ? 1 : 0)) * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
+    total += (1 + jsn) * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
     for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
     total += (size_t)spec_n * sizeof(float2) * (d == 3 ? 2 : 1);
     total += 5 * (size_t)nbmax * fe * sizeof(float);
@@ -414,6 +426,14 @@ static void set_unit_material(jfft_solver* h, double nu) {
     }
     h->jscale[a] = 1.0 / std::sqrt(h->kappa[a]);
   }
+  // On a grid with equal spacing the axes are equivalent and the unit diagonal is the
+  // same for every component; the mode form can round it differently per axis, so
+  // one value (axis 0's) is kept for all.
+  if (js_components(g, h->element) == 1)
+    for (int a = 1; a < d; ++a) {
+      h->kappa[a] = h->kappa[0];
+      h->jscale[a] = h->jscale[0];
+    }
 }
 
 // coarse: pixels per axis of a geometry G_p (NULL: the field has one value per voxel).
@@ -463,12 +483,17 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   }
   CK(launch_material(h->field, h->E, g.N, m->kind, m->e_min, m->e_max, m->exponent, h->st));
   CK(launch_node_esum(g, h->E, h->esum, h->st));
+  // resolved J^1/2 table: js[a jcs + node] = diag^-1/2 (void nodes: void_js)
+  const double* dsrc = h->esum;
+  int64_t dsrc_cs = 0;
   if (h->element == JFFT_ELEM_P1) {
     CK(launch_diag_p1(g, h->E, h->kappa_p1, h->x, h->st));   // x is free outside a solve
-    CK(launch_jacobi_half(h->x, h->js, 2 * g.N, h->st));
-  } else {
-    CK(launch_jacobi_half(h->esum, h->js, g.N, h->st));
+    dsrc = h->x;
+    dsrc_cs = g.N;
   }
+  const int jsn = js_components(g, h->element);
+  CK(launch_jacobi_half(dsrc, dsrc_cs, h->jscale, h->void_js, jsn, g.N, h->js,
+                        h->precision == JFFT_PREC_MIXED ? h->js32 : nullptr, h->st));
   double lam, mu;
   if (h->cref_mean) {
     int np = 0;
@@ -494,7 +519,6 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   if (s) return s;
   if (h->precision == JFFT_PREC_MIXED) {
     CK(launch_to_f32(h->E, h->E32, g.N, 1, nullptr, h->st));
-    CK(launch_to_f32(h->js, h->js32, g.N * (h->element == JFFT_ELEM_P1 ? 2 : 1), 1, nullptr, h->st));
     CK(launch_to_f32(h->G, h->G32, g.F * h->ds, 1, nullptr, h->st));
     for (int a = 0; a < g.d; ++a)
       CK(launch_to_f32(reinterpret_cast<const double*>(h->tw[a]), reinterpret_cast<float*>(h->tw32[a]), 2 * g.n[a], 1,
@@ -554,7 +578,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   if (o.element != JFFT_ELEM_Q1 && o.element != JFFT_ELEM_P1) return bail(fail(h, JFFT_ERR_ARG, "unknown element"));
   if (o.element == JFFT_ELEM_P1 && d != 2) return bail(fail(h, JFFT_ERR_UNSUPPORTED, "P1 triangles are 2D"));
   h->element = o.element;
-  h->jcs = h->element == JFFT_ELEM_P1 ? g.N : 0;
+  h->jcs = js_components(g, h->element) > 1 ? g.N : 0;
   // unit material and reference material
   set_unit_material(h, mat->nu);
   if (C_ref) {
@@ -611,7 +635,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->field, g.N * sizeof(double));
   AL(h->E, g.N * sizeof(double));
   AL(h->esum, g.N * sizeof(double));
-  AL(h->js, g.N * sizeof(double) * (h->element == JFFT_ELEM_P1 ? 2 : 1));
+  AL(h->js, g.N * sizeof(double) * js_components(g, h->element));
   AL(h->G, (size_t)g.F * h->ds * sizeof(double));
   for (int a = 0; a < d; ++a) AL(h->tw[a], (size_t)g.n[a] * sizeof(double2));
   AL(h->T, (size_t)spec_n * sizeof(double2));
@@ -632,7 +656,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->active, nbmax * sizeof(int));
   if (o.precision == JFFT_PREC_MIXED) {
     AL(h->E32, g.N * sizeof(float));
-    AL(h->js32, g.N * sizeof(float) * (h->element == JFFT_ELEM_P1 ? 2 : 1));
+    AL(h->js32, g.N * sizeof(float) * js_components(g, h->element));
     AL(h->G32, (size_t)g.F * h->ds * sizeof(float));
     for (int a = 0; a < d; ++a) AL(h->tw32[a], (size_t)g.n[a] * sizeof(float2));
     AL(h->T32, (size_t)spec_n * sizeof(float2));
@@ -750,18 +774,18 @@ static cudaError_t apply_op(jfft_solver* h, const Work<float>& w, const float* x
 static cudaError_t precond_op(jfft_solver* h, const Work<double>& w, int pc, const double* r, double* z, int nb,
                               CgState* cg, int* np, StageCtl sc = no_stage()) {
   if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
-    return launch_green_precond(h->g, w.pl, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js,
-                                pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg, h->st, sc, h->jcs);
-  return launch_jacobi_precond(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
-                               h->partial, np, cg, h->st, sc, h->jcs);
+    return launch_green_precond(h->g, w.pl, r, z, nb, field_elems(h), w.js, pc == JFFT_PC_GREEN_JACOBI, h->partial,
+                                np, cg, h->st, sc, h->jcs);
+  return launch_jacobi_precond(h->g, r, z, nb, field_elems(h), w.js, pc == JFFT_PC_NONE, h->partial, np, cg, h->st,
+                               sc, h->jcs);
 }
 static cudaError_t precond_op(jfft_solver* h, const Work<float>& w, int pc, const float* r, float* z, int nb,
                               CgState* cg, int* np, StageCtl sc = no_stage()) {
   if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI)
-    return launch_green_precond_f32(h->g, w.pl, r, z, nb, w.js, h->jscale, h->void_js, pc == JFFT_PC_GREEN_JACOBI,
-                                    h->partial, np, cg, h->st, sc, h->jcs);
-  return launch_jacobi_precond_f32(h->g, r, z, nb, field_elems(h), w.js, h->jscale, h->void_js, pc == JFFT_PC_NONE,
-                                   h->partial, np, cg, h->st, sc, h->jcs);
+    return launch_green_precond_f32(h->g, w.pl, r, z, nb, w.js, pc == JFFT_PC_GREEN_JACOBI, h->partial, np, cg,
+                                    h->st, sc, h->jcs);
+  return launch_jacobi_precond_f32(h->g, r, z, nb, field_elems(h), w.js, pc == JFFT_PC_NONE, h->partial, np, cg,
+                                   h->st, sc, h->jcs);
 }
 
 // Plan-time autotuner: times the candidate launch shapes of the working precision's
@@ -954,17 +978,21 @@ static bool loop_graph_ready(jfft_solver* h, const Work<T>& w, int nb, int pc, d
 // Runs PCG in working precision T on w.r (holding the right-hand side) from x = 0
 // for nb right-hand sides. The INIT_FF stage must have run on w.r.
 template <typename T>
+// keep: continue the recurrence of the previous call (reliable update): w.p and the
+// kept gamma carry over, the first direction is z + (r.z / gamma) p; the caller has
+// replaced w.r and started the states with kStageInitFFKeep.
 static jfft_status pcg_core_t(jfft_solver* h, const Work<T>& w, int nb, int pc, double tol, int stop_mode,
-                              int* status_out) {
+                              int* status_out, bool keep = false) {
   const Grid& g = h->g;
   const int64_t fe = field_elems(h);
   int np = 0;
   jfft_status s;
   CK(cudaMemsetAsync(w.x, 0, nb * fe * sizeof(T), h->st));
-  CK(cudaMemsetAsync(w.p, 0, nb * fe * sizeof(T), h->st));
+  if (!keep) CK(cudaMemsetAsync(w.p, 0, nb * fe * sizeof(T), h->st));
   CK(cudaMemsetAsync(h->stage_cnt, 0, nb * sizeof(unsigned), h->st));
   // Each scalar stage runs in the last block of the kernel that produces its partials.
-  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, StageCtl{kStageInitGamma, stop_mode, h->max_iter, tol, h->stage_cnt}));
+  CK(precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np,
+                StageCtl{keep ? kStageReplace : kStageInitGamma, stop_mode, h->max_iter, tol, h->stage_cnt}));
   CK(launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st));
   const int chunk = h->opt.check_every;
   int64_t launched = 0;
@@ -1012,6 +1040,14 @@ static jfft_status pcg_core(jfft_solver* h, int nb, int pc, double tol, int* sta
   return pcg_core_t<double>(h, work64(h), nb, pc, tol, h->opt.stop_mode, status_out);
 }
 
+// Reliable updates continue the FP32 recurrence across a residual replacement only
+// where ||r64 - r32|| <= kReliableGap ||r64||; a larger gap means the recurrence has
+// drifted from the true residual and its search direction is dropped (restart).
+#ifndef JFFT_RELIABLE_GAP
+#define JFFT_RELIABLE_GAP 0.1
+#endif
+constexpr double kReliableGap = JFFT_RELIABLE_GAP;
+
 // FP64 iterative refinement around the FP32 PCG (JFFT_PREC_MIXED). The right-hand
 // side is the macroscopic-strain load of h->shifts (macro) or the FP64 field f.
 // On return h->x holds u, its[b] the summed inner iterations, refine[b] the number
@@ -1051,7 +1087,15 @@ static jfft_status solve_mixed(jfft_solver* h, int nb, int pc, double tol, bool 
       CK(launch_sub_norm(g, f, h->q, h->r, nb, h->partial, &np, h->st));
     }
     CK(launch_reduce_partials(h->partial, np, nb, kMaxPartials, h->red, h->st));
-    CK(cudaMemcpyAsync(h->red_h, h->red, nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    // reliable updates: distance of the FP64 residual from the FP32 recurrence residual
+    // it is about to replace (rows nb .. 2 nb - 1 of the partial sums)
+    const bool cont = h->opt.reliable && k > 0;
+    if (cont) {
+      int npg = 0;
+      CK(launch_gap(g, h->r, w.r, nb, h->partial + (int64_t)nb * kMaxPartials, &npg, h->st));
+      CK(launch_reduce_partials(h->partial + (int64_t)nb * kMaxPartials, npg, nb, kMaxPartials, h->red + nb, h->st));
+    }
+    CK(cudaMemcpyAsync(h->red_h, h->red, (cont ? 2 : 1) * nb * sizeof(double), cudaMemcpyDeviceToHost, h->st));
     s = sync(h);
     if (s) return s;
     bool any = false;
@@ -1060,17 +1104,21 @@ static jfft_status solve_mixed(jfft_solver* h, int nb, int pc, double tol, bool 
       const double rr = h->red_h[b];
       const bool conv = ff[b] == 0.0 || (stop_mode == JFFT_STOP_REL ? rr <= tol * tol * ff[b] : rr <= tol);
       all_conv = all_conv && conv;
-      h->active_h[b] = (!conv && k < h->opt.max_refine) ? 1 : 0;
+      // 2: continue the recurrence (the replaced residual is within kReliableGap of the
+      // recurrence one); 1: restart it
+      const bool near = cont && h->red_h[nb + b] <= kReliableGap * kReliableGap * rr;
+      h->active_h[b] = (!conv && k < h->opt.max_refine) ? (near ? 2 : 1) : 0;
       any = any || h->active_h[b];
     }
     if (!any) break;
     CK(cudaMemcpyAsync(h->active, h->active_h, nb * sizeof(int), cudaMemcpyHostToDevice, h->st));
     CK(launch_to_f32(h->r, w.r, fe, nb, h->active, h->st));
     CK(launch_dot<float>(g, w.r, w.r, nb, fe, h->partial, &np, h->st));
-    CK(launch_cg_scalars(kStageInitFF, h->cg, h->partial, np, nb, h->opt.inner_tol, JFFT_STOP_REL, h->max_iter,
-                         h->st));
+    CK(launch_cg_scalars(cont ? kStageInitFFKeep : kStageInitFF, h->cg, h->partial, np, nb, h->opt.inner_tol,
+                         JFFT_STOP_REL, h->max_iter, h->st, h->active));
+    const bool keep = cont;
     int inner_status = kConverged;
-    s = pcg_core_t<float>(h, w, nb, pc, h->opt.inner_tol, JFFT_STOP_REL, &inner_status);
+    s = pcg_core_t<float>(h, w, nb, pc, h->opt.inner_tol, JFFT_STOP_REL, &inner_status, keep);
     if (s) return s;
     CK(launch_add_f32(h->x, w.x, nb * fe, h->st));
     for (int b = 0; b < nb; ++b)

@@ -170,9 +170,13 @@ cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* 
 cudaError_t launch_stress(const Grid& g, const ElemConst& ec, const double* E, const double* u, int nb,
                           const StrainShift* shifts, double* stress, double* partial, int* nparts, cudaStream_t st);
 
-// S5: esum[I] = sum of E over the 2^d voxels at node I; js = esum^-1/2 (0 for 0).
+// S5: esum[I] = sum of E over the 2^d voxels at node I.
 cudaError_t launch_node_esum(const Grid& g, const double* E, double* esum, cudaStream_t st);
-cudaError_t launch_jacobi_half(const double* esum, double* js, int64_t N, cudaStream_t st);
+// Resolved J^1/2 table, comps x N entries: entry (a, i) = ka[a] s^-1/2 for the diagonal
+// factor s = src[a src_cs + i] > 0, void_js where s = 0; FP64 into js and / or FP32
+// into js32 (either may be NULL).
+cudaError_t launch_jacobi_half(const double* src, int64_t src_cs, const double* ka, double void_js, int comps,
+                               int64_t N, double* js, float* js32, cudaStream_t st);
 // P1 voxels: diag[a][I] = sum over the 4 voxels around node I of E * kappa_o(a), o the
 // corner of that voxel at I (kappa4: [4 corners][2 components], corner c = o0 * 2 + o1).
 cudaError_t launch_diag_p1(const Grid& g, const double* E, const double* kappa4, double* diag, cudaStream_t st);
@@ -198,23 +202,21 @@ template <typename R> struct FftPlanT {
 using FftPlan = FftPlanT<double>;
 
 // S5 + S6: z_b = M^-1 r_b (Green, or Green-Jacobi when jacobi), with the partial
-// sums of r.z. jscale[a] = kappa_a^-1/2; void nodes use void_js.
+// sums of r.z. js: the resolved J^1/2 table, factor of DOF (a, node) at js[a jcs + node].
 cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* r, double* z, int nb,
-                                 int64_t field_stride, const double* js, const double* jscale, double void_js,
-                                 bool jacobi, double* partial, int* nparts, CgState* cg, cudaStream_t st,
-                                 StageCtl sc = no_stage(), int64_t jcs = 0);
+                                 int64_t field_stride, const double* js, bool jacobi, double* partial, int* nparts,
+                                 CgState* cg, cudaStream_t st, StageCtl sc = no_stage(), int64_t jcs = 0);
 // The same in FP32 (mixed-precision inner solve).
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
-                                     const float* js, const double* jscale, double void_js, bool jacobi,
-                                     double* partial, int* nparts, CgState* cg, cudaStream_t st,
-                                     StageCtl sc = no_stage(), int64_t jcs = 0);
+                                     const float* js, bool jacobi, double* partial, int* nparts, CgState* cg,
+                                     cudaStream_t st, StageCtl sc = no_stage(), int64_t jcs = 0);
 // Forward transform of nb d-component real fields -> line-major spectrum [nb][d][F].
 cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
                                     const double2** spec_out, cudaStream_t st);
 // z = J r (J = diag(K)^-1 with the void rule) or z = r (identity), partial r.z.
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
-                                  const double* jscale, double void_js, bool identity, double* partial, int* nparts,
-                                  CgState* cg, cudaStream_t st, StageCtl sc = no_stage(), int64_t jcs = 0);
+                                  bool identity, double* partial, int* nparts, CgState* cg, cudaStream_t st,
+                                  StageCtl sc = no_stage(), int64_t jcs = 0);
 
 // S4: CG vector updates and inner products (T = double or float; scalars in FP64).
 template <typename T>
@@ -227,9 +229,8 @@ cudaError_t launch_dot(const Grid& g, const T* a, const T* c, int nb, int64_t st
                        cudaStream_t st, CgState* cg = nullptr, StageCtl sc = no_stage());
 // FP32 variant of the Jacobi / identity preconditioner.
 cudaError_t launch_jacobi_precond_f32(const Grid& g, const float* r, float* z, int nb, int64_t stride, const float* js,
-                                      const double* jscale, double void_js, bool identity, double* partial,
-                                      int* nparts, CgState* cg, cudaStream_t st, StageCtl sc = no_stage(),
-                                      int64_t jcs = 0);
+                                      bool identity, double* partial, int* nparts, CgState* cg, cudaStream_t st,
+                                      StageCtl sc = no_stage(), int64_t jcs = 0);
 // Precision conversions for the refinement loop: dst = (float) src per rhs, zeroed
 // where active[b] == 0; u += (double) d; r = f - q with partial sums of r.r.
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n_per_rhs, int nb, const int* active, cudaStream_t st);
@@ -252,9 +253,20 @@ cudaError_t launch_cells(int n0, int n1, int n_cells, int n_loads, int kind, dou
                          const StrainShift* shifts, double tol, int stop_mode, int max_iter, int pc, double void_js,
                          double* u, double* chom, int* iters, double* rel_res, int* status, cudaStream_t st);
 
-enum ScalarStage { kStageInitFF = 0, kStageInitGamma = 1, kStageAlpha = 2, kStageRR = 3, kStageBeta = 4 };
+enum ScalarStage {
+  kStageInitFF = 0,
+  kStageInitGamma = 1,
+  kStageAlpha = 2,
+  kStageRR = 3,
+  kStageBeta = 4,
+  kStageInitFFKeep = 5,  // kStageInitFF that keeps gamma (a continued recurrence)
+  kStageReplace = 6      // first r.z after the residual was replaced: beta = v / gamma, gamma = v
+};
 cudaError_t launch_cg_scalars(int stage, CgState* cg, const double* partial, int nparts, int nb, double tol,
-                              int stop_mode, int max_iter, cudaStream_t st);
+                              int stop_mode, int max_iter, cudaStream_t st, const int* keep = nullptr);
+// Per right-hand side, partial sums of (r64 - r32)^2 (rows of kMaxPartials).
+cudaError_t launch_gap(const Grid& g, const double* r64, const float* r32, int nb, double* partial, int* nparts,
+                       cudaStream_t st);
 // out[row] = sum_j partial[row * pstride + j] in a fixed order.
 cudaError_t launch_reduce_partials(const double* partial, int nparts, int rows, int64_t pstride, double* out,
                                    cudaStream_t st);

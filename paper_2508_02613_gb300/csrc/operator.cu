@@ -714,16 +714,34 @@ cudaError_t launch_node_esum(const Grid& g, const double* E, double* esum, cudaS
   return cudaGetLastError();
 }
 
-__global__ void k_jacobi_half(const double* __restrict__ esum, double* __restrict__ js, int64_t N) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double s = esum[i];
-    js[i] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+// Resolved J^1/2 table (Sec. 3.2, J = diag(K)^-1, zero diagonals replaced by the void
+// value): for component a < comps and node i, with s the diagonal factor
+// src[a src_cs + i], j = s^-1/2 (0 where s = 0) and the entry is j ka[a], or void_js
+// where j = 0. Written in FP64 to js and / or in FP32 to js32 (the FP32 entry is
+// float(j) float(ka[a]), the product the FP32 kernels formed before the table was
+// resolved).
+struct Ka3 { double k[3]; };
+__global__ void k_jacobi_half(const double* __restrict__ src, int64_t src_cs, Ka3 ka, double void_js, int comps,
+                              int64_t N, double* __restrict__ js, float* __restrict__ js32) {
+  const int64_t n = comps * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(idx / N);
+    const int64_t i = idx - a * N;
+    const double s = src[a * src_cs + i];
+    const double j = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    if (js) js[idx] = j > 0.0 ? j * ka.k[a] : void_js;
+    if (js32) {
+      const float jf = (float)j;
+      js32[idx] = jf > 0.f ? jf * (float)ka.k[a] : (float)void_js;
+    }
   }
 }
 
-cudaError_t launch_jacobi_half(const double* esum, double* js, int64_t N, cudaStream_t st) {
-  const int blocks = (int)std::min<int64_t>((N + 255) / 256, 152 * 16);
-  JFFT_K("jacobi_half", st, k_jacobi_half<<<blocks, 256, 0, st>>>(esum, js, N));
+cudaError_t launch_jacobi_half(const double* src, int64_t src_cs, const double* ka, double void_js, int comps,
+                               int64_t N, double* js, float* js32, cudaStream_t st) {
+  Ka3 k3 = {{ka[0], ka[1], ka[2]}};
+  const int blocks = (int)std::min<int64_t>((comps * N + 255) / 256, 152 * 16);
+  JFFT_K("jacobi_half", st, k_jacobi_half<<<blocks, 256, 0, st>>>(src, src_cs, k3, void_js, comps, N, js, js32));
   return cudaGetLastError();
 }
 

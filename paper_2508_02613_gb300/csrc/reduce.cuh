@@ -53,6 +53,9 @@ __device__ __forceinline__ double block_sum(double v) {
 __device__ __forceinline__ void apply_stage(CgState& s, int stage, double v, double tol, int stop_mode, int max_iter) {
   switch (stage) {
     case kStageInitFF:
+    case kStageInitFFKeep: {
+      // a continued recurrence keeps gamma (the last r.z) unless its previous run broke down
+      const bool keep = stage == kStageInitFFKeep && s.done != kBreakdown && s.gamma > 0.0 && isfinite(s.gamma);
       s.ff = v;
       s.rr = v;
       s.rr_stop = stop_mode == 0 ? tol * tol * v : tol;
@@ -60,9 +63,16 @@ __device__ __forceinline__ void apply_stage(CgState& s, int stage, double v, dou
       s.max_iter = max_iter;
       s.alpha = 0.0;
       s.beta = 0.0;
-      s.gamma = 0.0;
+      if (!keep) s.gamma = 0.0;
       s.done = (v == 0.0 || v <= s.rr_stop) ? kConverged : kRunning;
       if (!isfinite(v)) s.done = kBreakdown;
+      break;
+    }
+    case kStageReplace:
+      // beta = 0 (a fresh start, p = z) where no gamma was kept
+      s.beta = s.gamma > 0.0 ? v / s.gamma : 0.0;
+      s.gamma = v;
+      if (!(v > 0.0) || !isfinite(v)) s.done = kBreakdown;
       break;
     case kStageInitGamma:
       s.gamma = v;
@@ -116,7 +126,7 @@ __device__ __forceinline__ double canonical_sum(const double* p, int n) {
 // every block has stored the block's partial at partial_row[slot]. The block that
 // arrives last for right-hand side b (atomic counter) sums partial_row[0..nblocks)
 // with canonical_sum and applies the stage to cg[b] (skipped for a right-hand side
-// that is done, except at kStageInitFF), then re-arms the counter. Every thread
+// that is done, except at the two InitFF stages), then re-arms the counter. Every thread
 // of the block must call it.
 __device__ __forceinline__ void fused_stage_tail(const StageCtl& sc, CgState* cg, int b, const double* partial_row,
                                                  int nblocks) {
@@ -133,7 +143,8 @@ __device__ __forceinline__ void fused_stage_tail(const StageCtl& sc, CgState* cg
   __threadfence();
   const double v = canonical_sum(partial_row, nblocks);
   if (threadIdx.x == 0) {
-    if (sc.stage == kStageInitFF || !cg[b].done) apply_stage(cg[b], sc.stage, v, sc.tol, sc.stop_mode, sc.max_iter);
+    if (sc.stage == kStageInitFF || sc.stage == kStageInitFFKeep || !cg[b].done)
+      apply_stage(cg[b], sc.stage, v, sc.tol, sc.stop_mode, sc.max_iter);
     sc.cnt[b] = 0u;
   }
 }

@@ -50,11 +50,15 @@ def test_fp32_operator_and_preconditioners(shape):
 
 @pytest.mark.parametrize("pc", ["green", "green_jacobi"])
 @pytest.mark.parametrize("tol", [1e-8, 1e-11])
-def test_mixed_solve_reaches_fp64_residual(pc, tol):
+@pytest.mark.parametrize("reliable", [False, True])
+def test_mixed_solve_reaches_fp64_residual(pc, tol, reliable):
+    """reliable: the FP32 recurrence continues across residual replacements (inner
+    tolerance 0.1, so that the recurrence stays close to the true residual and is
+    continued rather than restarted)."""
     shape = (32, 32)
     rho = smooth_density(shape, 16, 4.0, 0)
     E = material.young_from_density(rho, 1e-4, 1.0, 2.0)
-    s = _solver(shape, rho)
+    s = _solver(shape, rho, reliable=reliable, inner_tol=0.1 if reliable else 1e-3)
     eps = mandel_unit_loads(2)
     out = s.solve(eps, tol, pc)
     assert out["status"] == 0
