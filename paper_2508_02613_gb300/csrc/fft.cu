@@ -77,7 +77,7 @@ template <typename T> __device__ __forceinline__ cplx<T> jpair(const T* __restri
 // Pass A: forward FFT along contiguous rows, written transposed.
 // in: [S][R][Lin] (real or complex); out: [S][Lout][R]. w rows per block, TPL lanes
 // per row (block = w * TPL threads).
-template <typename T, bool REAL, bool JAC>
+template <typename T, bool REAL, bool JAC, int LC>
 __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_rows_fwd(int D, const T* __restrict__ rin, const cplx<T>* __restrict__ cin,
                                                   cplx<T>* __restrict__ out, int R, int Lin, int lgTPL, int lgw,
                                                   const cplx<T>* __restrict__ tw, const T* __restrict__ js,
@@ -90,12 +90,13 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
   if (cg && cg[S / slabs_per_b].done) return;
   const int w = 1 << lgw;
   const int r0 = blockIdx.x * w;
-  const int L = REAL ? Lin / 2 : Lin;
+  if (LC) Lin = REAL ? 2 * LC : LC;
+  const int L = LC ? LC : (REAL ? Lin / 2 : Lin);
   const int Lout = REAL ? L + 1 : L;
   const int ls = line_slots(L);
-  const int TPL = 1 << lgTPL;
+  const int TPL = LC ? LC / RM : 1 << lgTPL;
   const int RME = L < RM ? L : RM;
-  const int line = threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
+  const int line = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
   // twiddle table of the axis (Lin entries) in shared memory; the engine's first
   // barrier orders these stores before any use
   C* twl = sm2;
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
       v[r] = x;
     }
   }
-  C* res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, twl, REAL ? 2 : 1);
+  C* res;
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC, REAL ? 2 : 1>(v, j, A + line * ls, B + line * ls, twl);
+  else res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, twl, REAL ? 2 : 1);
   res -= line * ls;  // back to the block's buffer base
   if (REAL) {
     // X[k] = (Z[k] + conj Z[M-k]) - i W^k (Z[k] - conj Z[M-k]), k = 0..M (times 2);
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
 // Pass C: contiguous lines of axis 0 for all d components of one frequency line:
 // forward FFT, block multiply by the stored symbol, inverse FFT (or forward only).
 // Block = D * TPL threads; lanes [a TPL, (a+1) TPL) transform component a.
-template <typename T, int D, bool GREEN>
+template <typename T, int D, bool GREEN, int LC>
 __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __restrict__ spec, int nlines, int L, int lgTPL,
                                                const cplx<T>* __restrict__ tw, const T* __restrict__ G,
                                                const CgState* __restrict__ cg) {
@@ -158,10 +161,11 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
   C* sm2 = reinterpret_cast<C*>(sm_raw);
   const int l = blockIdx.x, b = blockIdx.y;
   if (cg && cg[b].done) return;
+  if (LC) L = LC;
   const int ls = line_slots(L);
-  const int TPL = 1 << lgTPL;
+  const int TPL = LC ? LC / RM : 1 << lgTPL;
   const int RME = L < RM ? L : RM;
-  const int a = threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
+  const int a = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
   C* twl = sm2;  // twiddle table (L entries), ordered by the engine's first barrier
   for (int i = threadIdx.x; i < L; i += blockDim.x) twl[i] = tw[i];
   C* A = sm2 + L;
@@ -171,7 +175,9 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
 #pragma unroll
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = gline[j + TPL * r];
-  C* res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, twl, 1) - a * ls;
+  C* res;
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC, 1>(v, j, A + a * ls, B + a * ls, twl) - a * ls;
+  else res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, twl, 1) - a * ls;
   if (GREEN) {
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
       const T* gk = G + ((int64_t)l * L + k) * NCMP;
@@ -200,7 +206,8 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
       if (r < RME) v[r] = res[a * ls + spad(j + TPL * r)];
     C* other = (res == A) ? B : A;
     // stage 1 writes `other` first, so no lane overwrites values still being read from res
-    res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, twl, 1) - a * ls;
+    if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC, 1>(v, j, other + a * ls, res + a * ls, twl) - a * ls;
+    else res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, twl, 1) - a * ls;
   }
   C* gout = spec + (((int64_t)b * D + a) * nlines + l) * L;
 #pragma unroll
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
 // Pass B: inverse FFT along rows whose frequencies are stored transposed.
 // in: [S][Lin][R]; out: [S][R][Lout] (real: Lout = 2 (Lin - 1), with J^1/2 and the
 // r . z partial; complex: Lout = Lin). w rows per block, TPL lanes per row.
-template <typename T, bool REAL, bool JAC>
+template <typename T, bool REAL, bool JAC, int LC>
 __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_cols_inv(int D, const cplx<T>* __restrict__ in, T* __restrict__ rout,
                                                   cplx<T>* __restrict__ cout, int R, int Lin, int lgTPL, int lgw,
                                                   const cplx<T>* __restrict__ tw, const T* __restrict__ js,
@@ -230,11 +237,12 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
   if (cg && cg[b].done) return;
   const int w = 1 << lgw;
   const int r0 = blockIdx.x * w;
-  const int L = REAL ? Lin - 1 : Lin;
+  if (LC) Lin = REAL ? LC + 1 : LC;
+  const int L = LC ? LC : (REAL ? Lin - 1 : Lin);
   const int ls = line_slots(L);
-  const int TPL = 1 << lgTPL;
+  const int TPL = LC ? LC / RM : 1 << lgTPL;
   const int RME = L < RM ? L : RM;
-  const int line = threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
+  const int line = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
   const int ntw = REAL ? 2 * L : L;  // twiddle table of the axis in shared memory
   C* twl = sm2;
   for (int i = threadIdx.x; i < ntw; i += blockDim.x) twl[i] = tw[i];
@@ -264,7 +272,9 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
 #pragma unroll
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = A[line * ls + spad(j + TPL * r)];
-  C* res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, twl, REAL ? 2 : 1) - line * ls;
+  C* res;
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC, REAL ? 2 : 1>(v, j, B + line * ls, A + line * ls, twl) - line * ls;
+  else res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, twl, REAL ? 2 : 1) - line * ls;
   if (REAL) {
     T dot = T(0);
     const int n = 2 * L;
@@ -324,6 +334,23 @@ template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {
 
 template <typename T> static const char* nm(const char* d64, const char* d32) { return sizeof(T) == 8 ? d64 : d32; }
 
+// Kernel instance for line length L: the engine's compile-time form for the lengths of
+// the usual grids (64 .. 2048), the runtime form otherwise.
+#define JFFT_LC_SWITCH(L, KERNEL, ...)                 \
+  switch (L) {                                         \
+    case 64: return KERNEL<__VA_ARGS__, 64>;           \
+    case 128: return KERNEL<__VA_ARGS__, 128>;         \
+    case 256: return KERNEL<__VA_ARGS__, 256>;         \
+    case 512: return KERNEL<__VA_ARGS__, 512>;         \
+    case 1024: return KERNEL<__VA_ARGS__, 1024>;       \
+    case 2048: return KERNEL<__VA_ARGS__, 2048>;       \
+    default: return KERNEL<__VA_ARGS__, 0>;            \
+  }
+template <typename T, bool REAL, bool JAC> static auto rows_kernel(int L) { JFFT_LC_SWITCH(L, k_rows_fwd, T, REAL, JAC) }
+template <typename T, bool REAL, bool JAC> static auto cols_kernel(int L) { JFFT_LC_SWITCH(L, k_cols_inv, T, REAL, JAC) }
+template <typename T, int D, bool GREEN> static auto lines_kernel(int L) { JFFT_LC_SWITCH(L, k_lines, T, D, GREEN) }
+#undef JFFT_LC_SWITCH
+
 // Real rows (last axis) forward, S = nb * d slabs.
 template <typename T>
 static cudaError_t pass_rows_real_fwd(const Grid& g, const FftPlanT<T>& p, const T* r, int nb, bool jac, const T* js,
@@ -335,7 +362,7 @@ static cudaError_t pass_rows_real_fwd(const Grid& g, const FftPlanT<T>& p, const
   const size_t smem = rows_smem<T>(L, w, Lin);
   dim3 grid(R / w, nb * g.d);
   const int tpl = lanes_per_line<T>(L);
-  auto k = jac ? k_rows_fwd<T, true, true> : k_rows_fwd<T, true, false>;
+  auto k = jac ? rows_kernel<T, true, true>(L) : rows_kernel<T, true, false>(L);
   JFFT_TRY(set_smem(k, smem));
   JFFT_K(nm<T>("fft_rows_real_fwd", "fft_rows_real_fwd_f32"), st,
          k<<<grid, w * tpl, smem, st>>>(g.d, r, nullptr, p.T, R, Lin, ilog2(tpl), ilog2(w), p.tw[g.d - 1], js, jsc, cg, g.d));
@@ -351,7 +378,7 @@ static cudaError_t pass_rows_cplx_fwd(const Grid& g, const FftPlanT<T>& p, int n
   const int slabs = nb * g.d * (g.M + 1);
   dim3 grid(R / w, slabs);
   const int tpl = lanes_per_line<T>(Lin);
-  auto k = k_rows_fwd<T, false, false>;
+  auto k = rows_kernel<T, false, false>(Lin);
   JFFT_TRY(set_smem(k, smem));
   JScaleT<T> jsc = {};
   JFFT_K(nm<T>("fft_rows_cplx_fwd", "fft_rows_cplx_fwd_f32"), st,
@@ -371,11 +398,11 @@ static cudaError_t pass_lines(const Grid& g, const FftPlanT<T>& p, int nb, bool 
   dim3 grid(nlines, nb);
   const char* name = green ? nm<T>("fft_lines", "fft_lines_f32") : nm<T>("fft_lines_fwd", "fft_lines_fwd_f32");
   if (g.d == 2) {
-    auto k = green ? k_lines<T, 2, true> : k_lines<T, 2, false>;
+    auto k = green ? lines_kernel<T, 2, true>(L) : lines_kernel<T, 2, false>(L);
     JFFT_TRY(set_smem(k, smem));
     JFFT_K(name, st, k<<<grid, 2 * tpl, smem, st>>>(spec, nlines, L, ilog2(tpl), p.tw[0], p.G, cg));
   } else {
-    auto k = green ? k_lines<T, 3, true> : k_lines<T, 3, false>;
+    auto k = green ? lines_kernel<T, 3, true>(L) : lines_kernel<T, 3, false>(L);
     JFFT_TRY(set_smem(k, smem));
     JFFT_K(name, st, k<<<grid, 3 * tpl, smem, st>>>(spec, nlines, L, ilog2(tpl), p.tw[0], p.G, cg));
   }
@@ -391,7 +418,7 @@ static cudaError_t pass_cols_cplx_inv(const Grid& g, const FftPlanT<T>& p, int n
   const int slabs = nb * g.d * (g.M + 1);
   dim3 grid(R / w, slabs);
   const int tpl = lanes_per_line<T>(Lin);
-  auto k = k_cols_inv<T, false, false>;
+  auto k = cols_kernel<T, false, false>(Lin);
   JFFT_TRY(set_smem(k, smem));
   JScaleT<T> jsc = {};
   JFFT_K(nm<T>("fft_cols_cplx_inv", "fft_cols_cplx_inv_f32"), st,
@@ -411,7 +438,7 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
   const size_t smem = rows_smem<T>(L, w, n);
   dim3 grid(R / w, nb * g.d);
   const int tpl = lanes_per_line<T>(L);
-  auto k = jac ? k_cols_inv<T, true, true> : k_cols_inv<T, true, false>;
+  auto k = jac ? cols_kernel<T, true, true>(L) : cols_kernel<T, true, false>(L);
   JFFT_TRY(set_smem(k, smem));
   JFFT_K(nm<T>("fft_cols_real_inv", "fft_cols_real_inv_f32"), st,
          k<<<grid, w * tpl, smem, st>>>(g.d, p.T, z, nullptr, R, L + 1, ilog2(tpl), ilog2(w), p.tw[g.d - 1], js, jsc, r,

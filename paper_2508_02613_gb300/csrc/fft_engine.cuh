@@ -175,4 +175,35 @@ __device__ cplx<T>* line_fft(cplx<T>* v, int j, int L, cplx<T>* b0, cplx<T>* b1,
   return cur;
 }
 
+// The same FFT with the line length L (>= RM) and the twiddle stride TWS known at
+// compile time: the stages unroll with constant radix, Stockham stride and twiddle
+// step, so the per-access index arithmetic folds into shifts and masks of the lane
+// index j (the runtime form spends more issue slots on integer work than on the
+// butterflies).
+template <typename T, int RM, bool INV, int L, int TWS, int NS>
+__device__ __forceinline__ void line_stages_ct(cplx<T>*& cur, cplx<T>*& nxt, cplx<T>* v, int j,
+                                               const cplx<T>* __restrict__ tw) {
+  if constexpr (NS < L) {
+    constexpr int R = (L / NS) >= RM ? RM : (L / NS);
+    fft_stage<T, RM, R, INV, false>(cur, nxt, v, j, L / RM, L, NS, tw, TWS);
+    cplx<T>* t = cur;
+    cur = nxt;
+    nxt = t;
+    __syncthreads();
+    line_stages_ct<T, RM, INV, L, TWS, NS * R>(cur, nxt, v, j, tw);
+  }
+}
+
+template <typename T, int RM, bool INV, int L, int TWS>
+__device__ __forceinline__ cplx<T>* line_fft_ct(cplx<T>* v, int j, cplx<T>* b0, cplx<T>* b1,
+                                                const cplx<T>* __restrict__ tw) {
+  static_assert(L >= RM, "compile-time lines hold at least one radix-RM butterfly per lane");
+  cplx<T>* cur = b0;
+  cplx<T>* nxt = b1;
+  fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, L / RM, L, 1, tw, TWS);
+  __syncthreads();
+  line_stages_ct<T, RM, INV, L, TWS, RM>(cur, nxt, v, j, tw);
+  return cur;
+}
+
 }  // namespace jfft
