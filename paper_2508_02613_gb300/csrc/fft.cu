@@ -99,8 +99,18 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
   const int line = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
   // twiddle table of the axis (Lin entries) in shared memory; the engine's first
   // barrier orders these stores before any use
+  // runtime length: the axis table; compile-time length: the post-pass twiddles
+  // (k <= L/2) followed by the engine's per-stage tables
   C* twl = sm2;
-  for (int i = threadIdx.x; i < Lin; i += blockDim.x) twl[i] = tw[i];
+  C* tst = twl;
+  if constexpr (LC > 0) {
+    const int npost = REAL ? L / 2 + 1 : 0;
+    for (int i = threadIdx.x; i < npost; i += blockDim.x) twl[i] = tw[i];
+    tst = twl + npost;
+    fill_stage_twiddles<T, RM, LC, REAL ? 2 : 1>(tst, tw);
+  } else {
+    for (int i = threadIdx.x; i < Lin; i += blockDim.x) twl[i] = tw[i];
+  }
   C* A = sm2 + Lin;
   C* B = A + w * ls;
   const int64_t row = r0 + line;
@@ -124,7 +134,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
     }
   }
   C* res;
-  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC, REAL ? 2 : 1>(v, j, A + line * ls, B + line * ls, twl);
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC>(v, j, A + line * ls, B + line * ls, tst);
   else res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, twl, REAL ? 2 : 1);
   res -= line * ls;  // back to the block's buffer base
   if (REAL) {
@@ -166,8 +176,12 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
   const int TPL = LC ? LC / RM : 1 << lgTPL;
   const int RME = L < RM ? L : RM;
   const int a = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
-  C* twl = sm2;  // twiddle table (L entries), ordered by the engine's first barrier
-  for (int i = threadIdx.x; i < L; i += blockDim.x) twl[i] = tw[i];
+  // twiddles (the axis table, or the per-stage tables of a compile-time length), ordered
+  // by the engine's first barrier
+  C* twl = sm2;
+  if constexpr (LC > 0) fill_stage_twiddles<T, RM, LC, 1>(twl, tw);
+  else
+    for (int i = threadIdx.x; i < L; i += blockDim.x) twl[i] = tw[i];
   C* A = sm2 + L;
   C* B = A + D * ls;
   const C* gline = spec + (((int64_t)b * D + a) * nlines + l) * L;
@@ -176,7 +190,7 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = gline[j + TPL * r];
   C* res;
-  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC, 1>(v, j, A + a * ls, B + a * ls, twl) - a * ls;
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC>(v, j, A + a * ls, B + a * ls, twl) - a * ls;
   else res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, twl, 1) - a * ls;
   if (GREEN) {
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
       if (r < RME) v[r] = res[a * ls + spad(j + TPL * r)];
     C* other = (res == A) ? B : A;
     // stage 1 writes `other` first, so no lane overwrites values still being read from res
-    if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC, 1>(v, j, other + a * ls, res + a * ls, twl) - a * ls;
+    if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC>(v, j, other + a * ls, res + a * ls, twl) - a * ls;
     else res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, twl, 1) - a * ls;
   }
   C* gout = spec + (((int64_t)b * D + a) * nlines + l) * L;
@@ -244,8 +258,18 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
   const int RME = L < RM ? L : RM;
   const int line = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
   const int ntw = REAL ? 2 * L : L;  // twiddle table of the axis in shared memory
+  // runtime length: the axis table; compile-time length: the pre-pass twiddles
+  // (k <= L/2) followed by the engine's per-stage tables
   C* twl = sm2;
-  for (int i = threadIdx.x; i < ntw; i += blockDim.x) twl[i] = tw[i];
+  C* tst = twl;
+  if constexpr (LC > 0) {
+    const int npost = REAL ? L / 2 + 1 : 0;
+    for (int i = threadIdx.x; i < npost; i += blockDim.x) twl[i] = tw[i];
+    tst = twl + npost;
+    fill_stage_twiddles<T, RM, LC, REAL ? 2 : 1>(tst, tw);
+  } else {
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) twl[i] = tw[i];
+  }
   C* A = sm2 + ntw;
   C* B = A + w * ls;
   for (int t = threadIdx.x; t < w * Lin; t += blockDim.x) {
@@ -273,7 +297,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = A[line * ls + spad(j + TPL * r)];
   C* res;
-  if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC, REAL ? 2 : 1>(v, j, B + line * ls, A + line * ls, twl) - line * ls;
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC>(v, j, B + line * ls, A + line * ls, tst) - line * ls;
   else res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, twl, REAL ? 2 : 1) - line * ls;
   if (REAL) {
     T dot = T(0);

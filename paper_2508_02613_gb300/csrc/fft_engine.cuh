@@ -175,34 +175,80 @@ __device__ cplx<T>* line_fft(cplx<T>* v, int j, int L, cplx<T>* b0, cplx<T>* b1,
   return cur;
 }
 
-// The same FFT with the line length L (>= RM) and the twiddle stride TWS known at
-// compile time: the stages unroll with constant radix, Stockham stride and twiddle
-// step, so the per-access index arithmetic folds into shifts and masks of the lane
-// index j (the runtime form spends more issue slots on integer work than on the
-// butterflies).
-template <typename T, int RM, bool INV, int L, int TWS, int NS>
-__device__ __forceinline__ void line_stages_ct(cplx<T>*& cur, cplx<T>*& nxt, cplx<T>* v, int j,
-                                               const cplx<T>* __restrict__ tw) {
+// The same FFT with the line length L (>= RM) known at compile time: the stages unroll
+// with constant radix, Stockham stride and twiddle step, so the per-access index
+// arithmetic folds into shifts and masks of the lane index j (the runtime form spends
+// more issue slots on integer work than on the butterflies). The twiddles come from
+// per-stage tables: the stage of span NS (> 1) and radix R keeps W_{NS R}^{r k}
+// (forward sign) at NS - RM + (r - 1) NS + k, k < NS, 1 <= r < R, L - RM entries in all.
+// Lanes read consecutive k there, where the strided reads of the axis table put up to
+// eight lanes of a warp on one shared-memory bank.
+template <int RM, int L, int NS> struct StageRadix {
+  static constexpr int R = (L / NS) >= RM ? RM : (L / NS);
+};
+
+// Fills the per-stage tables from the axis table tw_axis (exp(-2 pi i m / (L TWS))).
+template <typename T, int RM, int L, int TWS, int NS = RM>
+__device__ __forceinline__ void fill_stage_twiddles(cplx<T>* dst, const cplx<T>* __restrict__ tw_axis) {
   if constexpr (NS < L) {
-    constexpr int R = (L / NS) >= RM ? RM : (L / NS);
-    fft_stage<T, RM, R, INV, false>(cur, nxt, v, j, L / RM, L, NS, tw, TWS);
+    constexpr int R = StageRadix<RM, L, NS>::R;
+    for (int i = threadIdx.x; i < NS * (R - 1); i += blockDim.x) {
+      const int r = i / NS + 1, k = i % NS;
+      dst[NS - RM + i] = tw_axis[r * k * (L / (NS * R)) * TWS];
+    }
+    fill_stage_twiddles<T, RM, L, TWS, NS * R>(dst, tw_axis);
+  }
+}
+
+template <typename T, int RM, int R, bool INV, int L, int NS>
+__device__ __forceinline__ void fft_stage_ct(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int j,
+                                             const cplx<T>* __restrict__ tst) {
+  constexpr int TPL = L / RM;
+  constexpr int step = L / R;
+#pragma unroll
+  for (int i = 0; i < RM / R; ++i) {
+    const int b = j + TPL * i;
+    const int k = b & (NS - 1);
+    cplx<T> x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = src[spad(b + r * step)];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cplx<T> w = tst[NS - RM + (r - 1) * NS + k];
+      if (INV) w.y = -w.y;
+      x[r] = c_mul<T>(x[r], w);
+    }
+    Dft<T, R, INV>::run(x);
+    const int base = (b - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[spad(base + r * NS)] = x[r];
+  }
+}
+
+template <typename T, int RM, bool INV, int L, int NS>
+__device__ __forceinline__ void line_stages_ct(cplx<T>*& cur, cplx<T>*& nxt, int j, const cplx<T>* __restrict__ tst) {
+  if constexpr (NS < L) {
+    constexpr int R = StageRadix<RM, L, NS>::R;
+    fft_stage_ct<T, RM, R, INV, L, NS>(cur, nxt, j, tst);
     cplx<T>* t = cur;
     cur = nxt;
     nxt = t;
     __syncthreads();
-    line_stages_ct<T, RM, INV, L, TWS, NS * R>(cur, nxt, v, j, tw);
+    line_stages_ct<T, RM, INV, L, NS * R>(cur, nxt, j, tst);
   }
 }
 
-template <typename T, int RM, bool INV, int L, int TWS>
+// tst: the block's per-stage tables (fill_stage_twiddles), ordered before the call by
+// a barrier.
+template <typename T, int RM, bool INV, int L>
 __device__ __forceinline__ cplx<T>* line_fft_ct(cplx<T>* v, int j, cplx<T>* b0, cplx<T>* b1,
-                                                const cplx<T>* __restrict__ tw) {
+                                                const cplx<T>* __restrict__ tst) {
   static_assert(L >= RM, "compile-time lines hold at least one radix-RM butterfly per lane");
   cplx<T>* cur = b0;
   cplx<T>* nxt = b1;
-  fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, L / RM, L, 1, tw, TWS);
+  fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, L / RM, L, 1, nullptr, 1);
   __syncthreads();
-  line_stages_ct<T, RM, INV, L, TWS, RM>(cur, nxt, v, j, tw);
+  line_stages_ct<T, RM, INV, L, RM>(cur, nxt, j, tst);
   return cur;
 }
 
