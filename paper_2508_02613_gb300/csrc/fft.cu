@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
   if (LC) Lin = REAL ? 2 * LC : LC;
   const int L = LC ? LC : (REAL ? Lin / 2 : Lin);
   const int Lout = REAL ? L + 1 : L;
-  const int ls = line_slots(L);
+  const int ls = line_stride<T>(L, w);
   const int TPL = LC ? LC / RM : 1 << lgTPL;
   const int RME = L < RM ? L : RM;
   const int line = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
   const int r0 = blockIdx.x * w;
   if (LC) Lin = REAL ? LC + 1 : LC;
   const int L = LC ? LC : (REAL ? Lin - 1 : Lin);
-  const int ls = line_slots(L);
+  const int ls = line_stride<T>(L, w);
   const int TPL = LC ? LC / RM : 1 << lgTPL;
   const int RME = L < RM ? L : RM;
   const int line = LC ? (int)threadIdx.x / TPL : (int)threadIdx.x >> lgTPL, j = threadIdx.x & (TPL - 1);
@@ -340,12 +340,12 @@ static int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 template <typename T> static int rows_per_cta(int L, int R, int ntw) {
   const int tpl = lanes_per_line<T>(L);
   int w = std::max(1, FftOcc<T>::rows_threads / tpl);
-  while (w > 1 && ((size_t)2 * w * line_slots(L) + ntw) * sizeof(cplx<T>) > 98304) w >>= 1;
+  while (w > 1 && ((size_t)2 * w * line_stride<T>(L, w) + ntw) * sizeof(cplx<T>) > 98304) w >>= 1;
   while (w > R) w >>= 1;
   return w;
 }
 template <typename T> static size_t rows_smem(int L, int w, int ntw) {
-  return ((size_t)2 * w * line_slots(L) + ntw) * sizeof(cplx<T>);
+  return ((size_t)2 * w * line_stride<T>(L, w) + ntw) * sizeof(cplx<T>);
 }
 
 template <typename K> static cudaError_t set_smem(K kern, size_t bytes) {

@@ -21,6 +21,17 @@ namespace jfft {
 __host__ __device__ __forceinline__ int spad(int p) { return p + (p >> 4); }
 // Shared-memory slots of a line holding elements 0..n (inclusive).
 __host__ __device__ __forceinline__ int line_slots(int n) { return spad(n) + 1; }
+// Stride between the w lines of a row-pass block: at least line_slots(L); for 8-byte
+// elements on lines of 256 or more (a warp's lanes then work on one line in every
+// stage) also congruent to 32 / w modulo 16 slots, so that a warp reading or writing
+// element k of every line (the transposed input and output of the row passes: 32 / w
+// consecutive k on each of w lines) touches every bank pair exactly twice.
+template <typename T> __host__ __device__ __forceinline__ int line_stride(int L, int w) {
+  const int s = line_slots(L);
+  if (sizeof(cplx<T>) != 8 || L < 256 || w < 2 || w > 32) return s;
+  const int want = (32 / w) & 15;
+  return s + (((want - s) % 16) + 16) % 16;
+}
 
 template <typename T> __device__ __forceinline__ cplx<T> c_add(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ cplx<T> c_sub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
