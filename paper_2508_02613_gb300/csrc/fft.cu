@@ -272,9 +272,25 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
   }
   C* A = sm2 + ntw;
   C* B = A + w * ls;
-  for (int t = threadIdx.x; t < w * Lin; t += blockDim.x) {
-    const int k = t >> lgw, ln = t & (w - 1);
-    A[ln * ls + spad(k)] = in[((int64_t)S * Lin + k) * R + r0 + ln];
+  if constexpr (LC > 0) {
+    // all of a thread's transposed loads (ceil(Lin / TPL), whatever w) in flight at once
+    constexpr int PER = (LC + 1 + LC / RM - 1) / (LC / RM);
+    C buf[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int t = threadIdx.x + u * blockDim.x;
+      if (t < w * Lin) buf[u] = in[((int64_t)S * Lin + (t >> lgw)) * R + r0 + (t & (w - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int t = threadIdx.x + u * blockDim.x;
+      if (t < w * Lin) A[(t & (w - 1)) * ls + spad(t >> lgw)] = buf[u];
+    }
+  } else {
+    for (int t = threadIdx.x; t < w * Lin; t += blockDim.x) {
+      const int k = t >> lgw, ln = t & (w - 1);
+      A[ln * ls + spad(k)] = in[((int64_t)S * Lin + k) * R + r0 + ln];
+    }
   }
   __syncthreads();
   if (REAL) {
