@@ -138,6 +138,11 @@ typedef struct {
                                 for each load whose recurrence residual is within 10 % of it, the
                                 search direction is kept (beta from the last r.z) instead of
                                 restarting. */
+  int material_bf16;         /* MIXED: 1: the FP32 operator reads E from a BF16 copy (E rounded to 8
+                                significant bits, half the bytes of the FP32 copy); the FP64 residual
+                                of the refinement keeps the FP64 E, so the solve still meets its
+                                tolerance on the true operator. 0 (default): FP32 copy. Requires
+                                precision MIXED. */
 } jfft_options;
 
 typedef struct {

@@ -45,6 +45,7 @@ struct jfft_solver {
   // FP32 copies and vectors of the mixed-precision inner solve
   int precision = JFFT_PREC_FP64;
   float *E32 = nullptr, *js32 = nullptr, *G32 = nullptr;
+  void* E16 = nullptr;             // BF16 copy of E (options.material_bf16; E32 is then not allocated)
   float2* tw32[3] = {nullptr, nullptr, nullptr};
   float2 *T32 = nullptr, *U32 = nullptr;
   float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *z32 = nullptr;
@@ -257,6 +258,7 @@ extern "C" void jfft_default_options(jfft_options* o) {
   o->element = JFFT_ELEM_Q1;
   o->autotune = 0;
   o->reliable = 0;
+  o->material_bf16 = 0;
 }
 
 static jfft_status dalloc(jfft_solver* h, void** ptr, size_t bytes) {
@@ -341,7 +343,7 @@ static int js_components(const Grid& g, int element) {
 }
 
 // Device workspace of a solver (bytes), as allocated by jfft_create.
-static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int element = 0) {
+static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int element = 0, int material_bf16 = 0) {
   const int d = g.d;
   const int64_t fe = (int64_t)d * g.N;
   const int64_t spec_n = (int64_t)nbmax * d * g.F;
@@ -356,7 +358,7 @@ static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int el
   total += 1024 * sizeof(double) + nbmax * (sizeof(CgState) + sizeof(StrainShift) + sizeof(int) + sizeof(unsigned));
   total += sizeof(int);                                             // chunk counter
   if (precision == JFFT_PREC_MIXED) {
-    total += (1 + jsn) * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
+    total += (material_bf16 ? 2 : sizeof(float)) * g.N + jsn * g.N * sizeof(float) + (size_t)g.F * ds * sizeof(float);
     for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(float2);
     total += (size_t)spec_n * sizeof(float2) * (d == 3 ? 2 : 1);
     total += 5 * (size_t)nbmax * fe * sizeof(float);
@@ -518,7 +520,8 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
   s = build_symbol(h);
   if (s) return s;
   if (h->precision == JFFT_PREC_MIXED) {
-    CK(launch_to_f32(h->E, h->E32, g.N, 1, nullptr, h->st));
+    if (h->E16) CK(launch_to_bf16(h->E, h->E16, g.N, h->st));
+    else CK(launch_to_f32(h->E, h->E32, g.N, 1, nullptr, h->st));
     CK(launch_to_f32(h->G, h->G32, g.F * h->ds, 1, nullptr, h->st));
     for (int a = 0; a < g.d; ++a)
       CK(launch_to_f32(reinterpret_cast<const double*>(h->tw[a]), reinterpret_cast<float*>(h->tw32[a]), 2 * g.n[a], 1,
@@ -556,6 +559,8 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
     if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return bail(fail(h, JFFT_ERR_ARG, "inner_tol must lie in (0, 1)"));
     if (o.max_refine <= 0) return bail(fail(h, JFFT_ERR_ARG, "max_refine must be positive"));
   }
+  if (o.material_bf16 && o.precision != JFFT_PREC_MIXED)
+    return bail(fail(h, JFFT_ERR_ARG, "material_bf16 requires precision MIXED"));
   h->precision = o.precision;
   if (o.max_iter <= 0) return bail(fail(h, JFFT_ERR_ARG, "max_iter must be positive"));
   if (o.stop_mode != JFFT_STOP_REL && o.stop_mode != JFFT_STOP_ABS_SQ) return bail(fail(h, JFFT_ERR_ARG, "bad stop_mode"));
@@ -620,7 +625,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   const int nbmax = h->max_loads;
   const int64_t spec_n = (int64_t)nbmax * d * g.F;
   const size_t part_rows = (size_t)nbmax * 6;
-  const size_t total = plan_bytes(g, h->ds, nbmax, o.precision, h->element);
+  const size_t total = plan_bytes(g, h->ds, nbmax, o.precision, h->element, o.material_bf16);
   if (o.hbm_budget && total > o.hbm_budget) {
     char msg[160];
     snprintf(msg, sizeof msg, "workspace of %zu bytes exceeds hbm_budget %zu", total, o.hbm_budget);
@@ -655,7 +660,8 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->shifts, nbmax * sizeof(StrainShift));
   AL(h->active, nbmax * sizeof(int));
   if (o.precision == JFFT_PREC_MIXED) {
-    AL(h->E32, g.N * sizeof(float));
+    if (o.material_bf16) AL(h->E16, g.N * 2);
+    else AL(h->E32, g.N * sizeof(float));
     AL(h->js32, g.N * sizeof(float) * js_components(g, h->element));
     AL(h->G32, (size_t)g.F * h->ds * sizeof(float));
     for (int a = 0; a < d; ++a) AL(h->tw32[a], (size_t)g.n[a] * sizeof(float2));
@@ -768,6 +774,8 @@ static cudaError_t apply_op(jfft_solver* h, const Work<double>& w, const double*
 }
 static cudaError_t apply_op(jfft_solver* h, const Work<float>& w, const float* x, float* y, int nb, int dot, int* np,
                             CgState* cg, StageCtl sc = no_stage()) {
+  if (h->E16)
+    return launch_apply_K_f32_bf16(h->g, h->ec, h->E16, x, y, nb, field_elems(h), dot, h->partial, np, cg, h->st, sc);
   return launch_apply_K_f32(h->g, h->ec, w.E, x, y, nb, field_elems(h), dot, h->partial, np, cg, h->st, sc);
 }
 
@@ -1283,7 +1291,7 @@ extern "C" jfft_status jfft_apply_K(jfft_solver* h, int count, const double* x, 
   if (s) return s;
   if (h->precision == JFFT_PREC_MIXED) {
     CK(launch_to_f32(h->p, h->p32, count * fe, 1, nullptr, h->st));
-    CK(launch_apply_K_f32(h->g, h->ec, h->E32, h->p32, h->q32, count, fe, 0, nullptr, nullptr, nullptr, h->st));
+    CK(apply_op(h, work32(h), h->p32, h->q32, count, 0, nullptr, nullptr));
     CK(cudaMemsetAsync(h->q, 0, count * fe * sizeof(double), h->st));
     CK(launch_add_f32(h->q, h->q32, count * fe, h->st));
   } else {
@@ -1504,7 +1512,7 @@ extern "C" jfft_status jfft_workspace_estimate(const jfft_grid* grid, const jfft
   if (nbmax < g.d) nbmax = g.d;
   if (nbmax > kMaxLoads) return JFFT_ERR_ARG;
   if (o.precision != JFFT_PREC_FP64 && o.precision != JFFT_PREC_MIXED) return JFFT_ERR_ARG;
-  *bytes = plan_bytes(g, g.d * (g.d + 1) / 2, nbmax, o.precision, o.element);
+  *bytes = plan_bytes(g, g.d * (g.d + 1) / 2, nbmax, o.precision, o.element, o.material_bf16);
   return JFFT_OK;
 }
 

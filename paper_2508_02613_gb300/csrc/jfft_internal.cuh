@@ -164,6 +164,12 @@ cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const 
 cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* E, const float* x, float* y, int nb,
                                int64_t field_stride, int dot_mode, double* partial, int* nparts, CgState* cg,
                                cudaStream_t st, StageCtl sc = no_stage());
+// The same with E stored in BF16 (E16: N __nv_bfloat16 values), converted to FP32 on load.
+cudaError_t launch_apply_K_f32_bf16(const Grid& g, const ElemConst& ec, const void* E16, const float* x, float* y,
+                                    int nb, int64_t field_stride, int dot_mode, double* partial, int* nparts,
+                                    CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
+// E16 = E rounded to BF16 (round to nearest even), n values.
+cudaError_t launch_to_bf16(const double* E, void* E16, int64_t n, cudaStream_t st);
 
 // S8: element-averaged Mandel stress [nb][d*][N] (stress may be NULL) and partial
 // sums of vol * stress in partial[(b d* + s) * kMaxPartials + blk].

@@ -4,6 +4,7 @@
 // Alg. 2 combs (S5), and the Alg. 1 impulse / inversion steps (S9).
 #include "element.cuh"
 #include "reduce.cuh"
+#include <cuda_bf16.h>
 
 namespace jfft {
 
@@ -90,8 +91,15 @@ template <int D, typename T = double> static size_t march_smem(const MarchGeom& 
 // T: working precision of fields, material and constants (double or float); the
 // dot partial is accumulated per thread in T and across the block in double.
 // DOT: 0 none, 1 sum x.y, 2 sum y.y
-template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
-__global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConstT<T> ec, const T* __restrict__ E,
+// E in the working precision T, read from its stored type TE (T, or BF16 for the
+// mixed-precision operator with a BF16 material copy).
+template <typename T, typename TE> __device__ __forceinline__ T eload(const TE* __restrict__ E, int64_t i) {
+  if constexpr (std::is_same<TE, __nv_bfloat16>::value) return (T)__bfloat162float(E[i]);
+  else return (T)E[i];
+}
+
+template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT, typename TE = T>
+__global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConstT<T> ec, const TE* __restrict__ E,
                                                  T e_uniform, const T* __restrict__ x, T* __restrict__ y,
                                                  int64_t fstride, const StrainShift* __restrict__ shifts, T sgn,
                                                  double* __restrict__ partial, CgState* __restrict__ cg,
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
         const int h1 = idx / E2, h2 = idx % E2;
         const int gi1 = (i1s - 1 + h1 + n1) % n1;
         const int gi2 = (D == 3 ? (i2s - 1 + h2 + n2) % n2 : 0);
-        Es[idx] = E[(int64_t)l * plane + (int64_t)gi1 * n2 + gi2];
+        Es[idx] = eload<T>(E, (int64_t)l * plane + (int64_t)gi1 * n2 + gi2);
       }
     }
     __syncthreads();
@@ -224,9 +232,9 @@ constexpr int kWarpsPerCta2d = 4;
 // HAS_X = false: x = 0 (right-hand side); SHIFT: the load's macroscopic strain is added
 // to the element modes; the output is sgn * (K x + K_shift).
 // P1: the voxel is two linear triangles (tri_pair_force) instead of the Q1 element.
-template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, bool P1>
+template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, bool P1, typename TE = T>
 __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
-    k_apply_K2d(Grid g, ElemConstT<T> ec, const T* __restrict__ E, T e_uniform, const T* __restrict__ x,
+    k_apply_K2d(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
                 T* __restrict__ y, int64_t fstride, int seg, int groups, const StrainShift* __restrict__ shifts,
                 T sgn, double* __restrict__ partial, CgState* __restrict__ cg, StageCtl sc) {
   const int b = blockIdx.z;
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
         nh[a] = (HAS_X && lane == 31) ? xb[a * g.N + (int64_t)rown * n1 + cr] : T(0);
         carry[a] = T(0);
       }
-      if (HAS_E) En = E[(int64_t)row * n1 + c];
+      if (HAS_E) En = eload<T>(E, (int64_t)row * n1 + c);
     }
     for (int e0 = L0 - 1; e0 < L0 + seg; ++e0) {
       const T Ee = HAS_E ? En : e_uniform;
@@ -282,7 +290,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
             nh[a] = lane == 31 ? xb[a * g.N + (int64_t)rn2 * n1 + cr] : T(0);
           }
         }
-        if (HAS_E) En = E[(int64_t)re1 * n1 + c];
+        if (HAS_E) En = eload<T>(E, (int64_t)re1 * n1 + c);
       }
       T u[2][4];
 #pragma unroll
@@ -318,8 +326,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
   }
 }
 
-template <typename T, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false>
-static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x, T* y, int nb,
+template <typename T, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false, typename TE = T>
+static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const TE* E, T e_uniform, const T* x, T* y, int nb,
                                int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
                                StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
   const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
@@ -331,10 +339,10 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const T* 
                      : DOT == 1 ? "apply_K"
                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
   if (ec.elem == 1)
-    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true, TE><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
                          g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
   else
-    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false, TE><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
                          g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
@@ -365,9 +373,9 @@ constexpr int kWarpsPerCta3d = 4;
 #define JFFT_K3D_SEG 8
 #endif
 
-template <typename T, int J, int DOT, bool HAS_E, bool HAS_X, bool SHIFT>
+template <typename T, int J, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, typename TE = T>
 __global__ void __launch_bounds__(32 * kWarpsPerCta3d, JFFT_K3D_MINB)
-    k_apply_K3d(Grid g, ElemConstT<T> ec, const T* __restrict__ E, T e_uniform, const T* __restrict__ x,
+    k_apply_K3d(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
                 T* __restrict__ y, int64_t fstride, int seg, int groups2, int rowblocks,
                 const StrainShift* __restrict__ shifts, T sgn, double* __restrict__ partial,
                 CgState* __restrict__ cg, StageCtl sc) {
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta3d, JFFT_K3D_MINB)
           rhi1[a] = __shfl_down_sync(0xffffffffu, hi1[a], 1);
           if (lane == 31) { rhi0[a] = h0; rhi1[a] = h1; }
         }
-        const T Ee = HAS_E ? E[(b0 + (e1 & (n1 - 1))) * n2 + c] : e_uniform;
+        const T Ee = HAS_E ? eload<T>(E, (b0 + (e1 & (n1 - 1))) * n2 + c) : e_uniform;
         // corner index o0 * 4 + o1 * 2 + o2 (axis 0 is the highest bit)
         T u[3][8];
 #pragma unroll
@@ -470,8 +478,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta3d, JFFT_K3D_MINB)
   }
 }
 
-template <typename T, int J, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false>
-static cudaError_t apply_K3d_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x, T* y, int nb,
+template <typename T, int J, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false, typename TE = T>
+static cudaError_t apply_K3d_t(const Grid& g, const ElemConstT<T>& ec, const TE* E, T e_uniform, const T* x, T* y, int nb,
                                int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
                                StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
   const int groups2 = (g.n[2] + kWarpStride - 1) / kWarpStride;
@@ -484,7 +492,7 @@ static cudaError_t apply_K3d_t(const Grid& g, const ElemConstT<T>& ec, const T* 
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
                      : DOT == 1 ? "apply_K"
                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
-  JFFT_K(name, st, k_apply_K3d<T, J, DOT, HAS_E, HAS_X, SHIFT><<<grid, 32 * kWarpsPerCta3d, 0, st>>>(
+  JFFT_K(name, st, k_apply_K3d<T, J, DOT, HAS_E, HAS_X, SHIFT, TE><<<grid, 32 * kWarpsPerCta3d, 0, st>>>(
                        g, ec, E, e_uniform, x, y, fstride, seg, groups2, rowblocks, shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
@@ -508,13 +516,13 @@ template <int D> static MarchGeom march_geom(const Grid& g) {
   return m;
 }
 
-template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT>
-static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const T* E, T e_uniform, const T* x,
+template <typename T, int D, int DOT, bool HAS_X, bool HAS_E, bool SHIFT, typename TE = T>
+static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const TE* E, T e_uniform, const T* x,
                              T* y, int nb, int64_t fstride, const StrainShift* shifts, T sgn, double* partial,
                              int* nparts, CgState* cg, cudaStream_t st, StageCtl sc) {
   MarchGeom m = march_geom<D>(g);
   const size_t smem = march_smem<D, T>(m);
-  auto kern = k_apply_K<T, D, DOT, HAS_X, HAS_E, SHIFT>;
+  auto kern = k_apply_K<T, D, DOT, HAS_X, HAS_E, SHIFT, TE>;
   cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, nb);
@@ -600,24 +608,27 @@ cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const 
 
 // Working-precision FP32 operator (mixed-precision inner solve): y = K x with the
 // material in FP32, optional fused x.y partials (dot_mode 1) or none (0).
-template <int D>
-static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, const float* E, const float* x, float* y,
+template <int D, typename TE>
+static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, const TE* E, const float* x, float* y,
                                  int nb, int64_t fstride, int dot_mode, double* partial, int* nparts, CgState* cg,
                                  cudaStream_t st, StageCtl sc) {
   if (D == 2) {
-    if (dot_mode == 1) return apply_K2d_t<float, 1, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
-    return apply_K2d_t<float, 0, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
+    if (dot_mode == 1)
+      return apply_K2d_t<float, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
+    return apply_K2d_t<float, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
   }
   if (g.n[1] >= JFFT_K3D_J) {
     if (dot_mode == 1)
-      return apply_K3d_t<float, JFFT_K3D_J, 1, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
-    return apply_K3d_t<float, JFFT_K3D_J, 0, true>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
+      return apply_K3d_t<float, JFFT_K3D_J, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
+                                                                      cg, st, sc);
+    return apply_K3d_t<float, JFFT_K3D_J, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
+                                                                    cg, st, sc);
   }
   if (dot_mode == 1)
-    return apply_K_t<float, D, 1, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
-                                                    st, sc);
-  return apply_K_t<float, D, 0, true, true, false>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts, cg,
-                                                  st, sc);
+    return apply_K_t<float, D, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts,
+                                                         cg, st, sc);
+  return apply_K_t<float, D, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, nullptr, 1.f, partial, nparts,
+                                                       cg, st, sc);
 }
 
 cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* E, const float* x, float* y, int nb,
@@ -626,6 +637,27 @@ cudaError_t launch_apply_K_f32(const Grid& g, const ElemConst& ec, const float* 
   const ElemConstT<float> ecf = elem_const_as<float>(ec);
   if (g.d == 2) return apply_K_f32_d<2>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st, sc);
   return apply_K_f32_d<3>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st, sc);
+}
+
+cudaError_t launch_apply_K_f32_bf16(const Grid& g, const ElemConst& ec, const void* E16, const float* x, float* y,
+                                    int nb, int64_t field_stride, int dot_mode, double* partial, int* nparts,
+                                    CgState* cg, cudaStream_t st, StageCtl sc) {
+  const ElemConstT<float> ecf = elem_const_as<float>(ec);
+  const __nv_bfloat16* E = static_cast<const __nv_bfloat16*>(E16);
+  if (g.d == 2) return apply_K_f32_d<2>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st, sc);
+  return apply_K_f32_d<3>(g, ecf, E, x, y, nb, field_stride, dot_mode, partial, nparts, cg, st, sc);
+}
+
+// E16[i] = E[i] rounded to BF16 (round to nearest even)
+__global__ void k_to_bf16(const double* __restrict__ E, __nv_bfloat16* __restrict__ E16, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    E16[i] = __double2bfloat16(E[i]);
+}
+
+cudaError_t launch_to_bf16(const double* E, void* E16, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  JFFT_K("to_bf16", st, k_to_bf16<<<blocks, 256, 0, st>>>(E, static_cast<__nv_bfloat16*>(E16), n));
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ S8

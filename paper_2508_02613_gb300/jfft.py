@@ -41,7 +41,8 @@ class JfftOptions(ctypes.Structure):
     _fields_ = [("precision", c_int), ("max_iter", c_int), ("stop_mode", c_int), ("stream", c_void_p),
                 ("hbm_budget", c_size_t), ("check_every", c_int), ("io_memory", c_int), ("max_loads", c_int),
                 ("void_value", c_double), ("device", c_int), ("inner_tol", c_double), ("max_refine", c_int),
-                ("graphs", c_int), ("element", c_int), ("autotune", c_int), ("reliable", c_int)]
+                ("graphs", c_int), ("element", c_int), ("autotune", c_int), ("reliable", c_int),
+                ("material_bf16", c_int)]
 
 
 class JfftResult(ctypes.Structure):
@@ -183,7 +184,7 @@ class Solver:
     def __init__(self, shape, field, nu, kind="young", e_min=0.0, e_max=1.0, exponent=1.0, C_ref=None,
                  max_iter=100000, stop_mode="rel", stream=None, check_every=8, io="host", max_loads=6,
                  void_value=1.0, device=0, hbm_budget=0, pinned=False, precision="fp64", inner_tol=1e-3,
-                 max_refine=30, graphs=True, element="q1", autotune=False, reliable=False):
+                 max_refine=30, graphs=True, element="q1", autotune=False, reliable=False, material_bf16=False):
         self.lib = load()
         self.pinned = pinned
         self.shape = tuple(int(s) for s in shape)
@@ -213,6 +214,7 @@ class Solver:
         opt.element = ELEMENT[element]
         opt.autotune = 1 if autotune else 0
         opt.reliable = 1 if reliable else 0
+        opt.material_bf16 = 1 if material_bf16 else 0
         self.precision = precision
         self.max_loads = max(max_loads, self.d)
         h = c_void_p()

@@ -31,7 +31,7 @@ def test_status_strings_and_defaults(lib):
     assert opt.max_iter == 100000 and opt.check_every == 8 and opt.max_loads == 6
     assert opt.void_value == 1.0 and opt.io_memory == 0 and opt.stop_mode == 0
     assert opt.precision == 0 and opt.inner_tol == 1e-3 and opt.max_refine == 30 and opt.graphs == 1
-    assert opt.element == 0 and opt.autotune == 0 and opt.reliable == 0
+    assert opt.element == 0 and opt.autotune == 0 and opt.reliable == 0 and opt.material_bf16 == 0
 
 
 def test_sources_target_sm103a_only():

@@ -91,3 +91,62 @@ def test_mixed_solve_3d_and_rhs():
     assert r["status"] == 0
     u = r["u"][0] - r["u"][0].mean(axis=(1, 2, 3), keepdims=True)
     assert np.linalg.norm(f - assemble.apply(prob.K, u)) <= 1.01e-9 * np.linalg.norm(f)
+
+
+def bf16_round(x):
+    """Round to the nearest BF16 value (8 significant bits, ties to even), for normal
+    positive inputs: x = m 2^e with 0.5 <= m < 1, m rounded to a multiple of 2^-8."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0) / 256.0, e)
+
+
+def test_bf16_rounding_helper():
+    assert bf16_round(1.0) == 1.0 and bf16_round(1.0 + 2.0 ** -8) == 1.0       # tie -> even
+    assert bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2 * 2.0 ** -7               # tie -> even (up)
+    assert bf16_round(1.0 + 2.0 ** -7) == 1.0 + 2.0 ** -7                        # exact
+    assert bf16_round(0.3) == 0.30078125
+
+
+@pytest.mark.parametrize("shape", [(64, 512), (16, 16, 64)])
+def test_bf16_material_operator(shape):
+    """options.material_bf16: the FP32 operator equals the oracle's operator assembled
+    with E rounded to BF16 (to FP32 accuracy), and differs from the unrounded one by
+    the BF16 rounding of E."""
+    d = len(shape)
+    rho = smooth_density(shape, 8, 3.0, 1)
+    E = material.young_from_density(rho, 1e-4, 1.0, 2.0)
+    s = _solver(shape, rho, material_bf16=True)
+    x = random_field((2, d) + shape, 3)
+    got = s.apply_K(x)
+    prob16 = osolve.setup(shape, bf16_round(E), 0.3)
+    want16 = np.stack([assemble.apply(prob16.K, x[i]) for i in range(2)])
+    assert rel(got, want16) <= 2e-6
+    prob = osolve.setup(shape, E, 0.3)
+    want = np.stack([assemble.apply(prob.K, x[i]) for i in range(2)])
+    assert 1e-5 <= rel(got, want) <= 1e-2
+
+
+@pytest.mark.parametrize("pc", ["green", "green_jacobi"])
+@pytest.mark.parametrize("shape", [(32, 32), (8, 8, 16)])
+def test_bf16_material_solve_reaches_fp64_residual(pc, shape):
+    """The refinement's FP64 residual uses the FP64 E: the BF16 material copy changes
+    the inner solves only, and the solve meets 1e-9 on the true operator."""
+    d = len(shape)
+    rho = smooth_density(shape, 16 if d == 2 else 8, 4.0 if d == 2 else 3.0, 0)
+    E = material.young_from_density(rho, 1e-4, 1.0, 2.0)
+    s = _solver(shape, rho, material_bf16=True)
+    eps = mandel_unit_loads(d)
+    out = s.solve(eps, 1e-9, pc)
+    assert out["status"] == 0
+    assert np.all(out["rel_res"] <= 1e-9 * 1.01)
+    prob = osolve.setup(shape, E, 0.3)
+    ref = osolve.solve(prob, eps, 1e-13, pc)
+    assert rel(out["C_hom"], ref.C_hom) <= 1e-8
+    du = max(np.linalg.norm(out["u"][g] - ref.u[g]) / np.linalg.norm(ref.u[g]) for g in range(len(eps)))
+    assert du <= 1e4 * 1e-9, du
+
+
+def test_bf16_material_needs_mixed():
+    from paper_2508_02613_gb300.jfft import JfftError, Solver
+    with pytest.raises(JfftError):
+        Solver((16, 16), np.ones((16, 16)), 0.3, material_bf16=True)
