@@ -173,9 +173,9 @@ def traffic_bytes_per_unit(kernel, shape, d=2):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch with all three
 # loads active, from the ncu capture summarised in profiles/fp64_2d_1024_gj_kernels.md
-# (1024 x 1024, Green-Jacobi, contrast 1e4). Valid for the kernels of that capture; the
-# FP32 kernels have no current capture (their traffic stays null).
-NCU_TRAFFIC_PER_LAUNCH = {"apply_K": 59.59e6 + 9.87e6, "fft_lines": 63.12e6 + 1.11e6}
+# (1024 x 1024, Green-Jacobi, contrast 1e4), for kernels unchanged since that capture
+# (empty: every kernel has changed since; their traffic stays null).
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 
 def aggregate(ms_local, world, solves_per_step, dist=None, device=None):

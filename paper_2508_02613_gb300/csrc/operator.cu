@@ -227,13 +227,17 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
 // column c + 1 to lane l + 1 by a shuffle. Node (e0, c) is then complete for lanes
 // 1..31, so warps overlap by one column (stride 31): outputs o = 31 w + l, l >= 1.
 constexpr int kWarpStride = 31;
-constexpr int kWarpsPerCta2d = 4;
+// Warps per block: FP32 runs four-warp blocks; FP64 (bound by FP64 issue) runs one-warp
+// blocks, whose finer grid spreads the work evenly over the SMs (with four-warp blocks
+// the 1024^2 launch left the SMs idle for 12 % of its cycles; measured 367 -> 338 us per
+// 3-load launch).
+template <typename T> constexpr int k2d_warps() { return sizeof(T) == 8 ? 1 : 4; }
 
 // HAS_X = false: x = 0 (right-hand side); SHIFT: the load's macroscopic strain is added
 // to the element modes; the output is sgn * (K x + K_shift).
 // P1: the voxel is two linear triangles (tri_pair_force) instead of the Q1 element.
 template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, bool P1, typename TE = T>
-__global__ void __launch_bounds__(32 * kWarpsPerCta2d)
+__global__ void __launch_bounds__(32 * k2d_warps<T>())
     k_apply_K2d(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
                 T* __restrict__ y, int64_t fstride, int seg, int groups, const StrainShift* __restrict__ shifts,
                 T sgn, double* __restrict__ partial, CgState* __restrict__ cg, StageCtl sc) {
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta2d)
   if (SHIFT) sh = shifts[b];
   const int n0 = g.n[0], n1 = g.n[1];
   const int lane = threadIdx.x & 31;
-  const int grp = blockIdx.x * kWarpsPerCta2d + (threadIdx.x >> 5);
+  const int grp = blockIdx.x * k2d_warps<T>() + (threadIdx.x >> 5);
   const bool active_warp = grp < groups;
   const int o = grp * kWarpStride + lane;                  // output index before wrapping
   const int c = o % n1, cr = (o + 1) % n1;                 // own column, halo column (lane 31)
@@ -331,7 +335,7 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const TE*
                                int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
                                StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
   const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
-  const int ctas_x = (groups + kWarpsPerCta2d - 1) / kWarpsPerCta2d;
+  const int ctas_x = (groups + k2d_warps<T>() - 1) / k2d_warps<T>();
   int seg = std::min(g.n[0], g.tune[0] > 0 ? g.tune[0] : 16);
   while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
   dim3 grid(ctas_x, g.n[0] / seg, nb);
@@ -339,10 +343,10 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const TE*
                      : DOT == 1 ? "apply_K"
                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
   if (ec.elem == 1)
-    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true, TE><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true, TE><<<grid, 32 * k2d_warps<T>(), 0, st>>>(
                          g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
   else
-    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false, TE><<<grid, 32 * kWarpsPerCta2d, 0, st>>>(
+    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false, TE><<<grid, 32 * k2d_warps<T>(), 0, st>>>(
                          g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
