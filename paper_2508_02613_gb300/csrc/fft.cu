@@ -36,8 +36,12 @@ cudaError_t launch_twiddles(double2* tw, int n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T> __device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// 1 at run time for the engine's FP64 sums (see add1): the first entry of an axis twiddle
+// table is exp(0) = (1, 0) exactly; FP32 sums need no such value.
+template <typename T> __device__ __forceinline__ T runtime_one(const cplx<T>* __restrict__ tw) {
+  if constexpr (sizeof(T) == 8) return tw[0].x;
+  else return T(1);
+}
 template <typename T, bool INV> __device__ __forceinline__ cplx<T> twmul(cplx<T> v, cplx<T> w) {
   if (INV) w.y = -w.y;
   return mk<T>(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
@@ -134,8 +138,9 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
     }
   }
   C* res;
-  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC>(v, j, A + line * ls, B + line * ls, tst);
-  else res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, twl, REAL ? 2 : 1);
+  const T one = runtime_one<T>(tw);
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC>(v, j, A + line * ls, B + line * ls, tst, one);
+  else res = line_fft<T, RM, false>(v, j, L, A + line * ls, B + line * ls, twl, REAL ? 2 : 1, one);
   res -= line * ls;  // back to the block's buffer base
   if (REAL) {
     // X[k] = (Z[k] + conj Z[M-k]) - i W^k (Z[k] - conj Z[M-k]), k = 0..M (times 2);
@@ -143,11 +148,11 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
     C* z = res + line * ls;
     for (int k = j; k <= L / 2; k += TPL) {
       const C zk = z[spad(k)], zm = z[spad((L - k) & (L - 1))];
-      const C A_ = mk<T>(zk.x + zm.x, zk.y - zm.y);
-      const C B_ = mk<T>(zk.x - zm.x, zk.y + zm.y);
+      const C A_ = mk<T>(add1(zk.x, zm.x, one), sub1(zk.y, zm.y, one));
+      const C B_ = mk<T>(sub1(zk.x, zm.x, one), add1(zk.y, zm.y, one));
       const C Cw = twmul<T, false>(B_, twl[k]);
-      z[spad(k)] = mk<T>(A_.x + Cw.y, A_.y - Cw.x);
-      z[spad(L - k)] = mk<T>(A_.x - Cw.y, -A_.y - Cw.x);
+      z[spad(k)] = mk<T>(add1(A_.x, Cw.y, one), sub1(A_.y, Cw.x, one));
+      z[spad(L - k)] = mk<T>(sub1(A_.x, Cw.y, one), sub1(-A_.y, Cw.x, one));
     }
     __syncthreads();
   }
@@ -190,8 +195,9 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = gline[j + TPL * r];
   C* res;
-  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC>(v, j, A + a * ls, B + a * ls, twl) - a * ls;
-  else res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, twl, 1) - a * ls;
+  const T one = runtime_one<T>(tw);
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, false, LC>(v, j, A + a * ls, B + a * ls, twl, one) - a * ls;
+  else res = line_fft<T, RM, false>(v, j, L, A + a * ls, B + a * ls, twl, 1, one) - a * ls;
   if (GREEN) {
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
       const T* gk = G + ((int64_t)l * L + k) * NCMP;
@@ -220,8 +226,8 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
       if (r < RME) v[r] = res[a * ls + spad(j + TPL * r)];
     C* other = (res == A) ? B : A;
     // stage 1 writes `other` first, so no lane overwrites values still being read from res
-    if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC>(v, j, other + a * ls, res + a * ls, twl) - a * ls;
-    else res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, twl, 1) - a * ls;
+    if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC>(v, j, other + a * ls, res + a * ls, twl, one) - a * ls;
+    else res = line_fft<T, RM, true>(v, j, L, other + a * ls, res + a * ls, twl, 1, one) - a * ls;
   }
   C* gout = spec + (((int64_t)b * D + a) * nlines + l) * L;
 #pragma unroll
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
     }
   }
   __syncthreads();
+  const T one = runtime_one<T>(tw);
   if (REAL) {
     // Z[k] = E + i O, E = X[k] + conj X[M-k], O = (X[k] - conj X[M-k]) W^-k (times 2);
     // the lanes of each line take the pairs of their own line.
@@ -300,11 +307,11 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
     for (int k = j; k <= L / 2; k += TPL) {
       C xk = x[spad(k)], xm = x[spad(L - k)];
       if (k == 0) { xk.y = T(0); xm.y = T(0); }
-      const C E = mk<T>(xk.x + xm.x, xk.y - xm.y);
-      const C Bv = mk<T>(xk.x - xm.x, xk.y + xm.y);
+      const C E = mk<T>(add1(xk.x, xm.x, one), sub1(xk.y, xm.y, one));
+      const C Bv = mk<T>(sub1(xk.x, xm.x, one), add1(xk.y, xm.y, one));
       const C O = twmul<T, true>(Bv, twl[k]);
-      x[spad(k)] = mk<T>(E.x - O.y, E.y + O.x);
-      if (k != 0) x[spad(L - k)] = mk<T>(E.x + O.y, -E.y + O.x);
+      x[spad(k)] = mk<T>(sub1(E.x, O.y, one), add1(E.y, O.x, one));
+      if (k != 0) x[spad(L - k)] = mk<T>(add1(E.x, O.y, one), add1(-E.y, O.x, one));
     }
     __syncthreads();
   }
@@ -313,8 +320,8 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
   for (int r = 0; r < RM; ++r)
     if (r < RME) v[r] = A[line * ls + spad(j + TPL * r)];
   C* res;
-  if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC>(v, j, B + line * ls, A + line * ls, tst) - line * ls;
-  else res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, twl, REAL ? 2 : 1) - line * ls;
+  if constexpr (LC > 0) res = line_fft_ct<T, RM, true, LC>(v, j, B + line * ls, A + line * ls, tst, one) - line * ls;
+  else res = line_fft<T, RM, true>(v, j, L, B + line * ls, A + line * ls, twl, REAL ? 2 : 1, one) - line * ls;
   if (REAL) {
     T dot = T(0);
     const int n = 2 * L;

@@ -33,8 +33,24 @@ template <typename T> __host__ __device__ __forceinline__ int line_stride(int L,
   return s + (((want - s) % 16) + 16) % 16;
 }
 
-template <typename T> __device__ __forceinline__ cplx<T> c_add(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __device__ __forceinline__ cplx<T> c_sub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// Sums and differences. GB300 issues FP64 FMA at 1.19x the rate of FP64 add (probe: 0.596
+// vs 0.502 T instructions/s), so in FP64 a + b is formed as fma(a, one, b) with `one` = 1
+// read at run time (a literal 1 would be folded back into an add); the rounding is that
+// of a + b. FP32 adds and FMAs issue at the same rate.
+template <typename T> __device__ __forceinline__ T add1(T a, T b, T one) {
+  if constexpr (sizeof(T) == 8) return fma(a, one, b);
+  else return a + b;
+}
+template <typename T> __device__ __forceinline__ T sub1(T a, T b, T one) {
+  if constexpr (sizeof(T) == 8) return fma(b, -one, a);
+  else return a - b;
+}
+template <typename T> __device__ __forceinline__ cplx<T> c_add(cplx<T> a, cplx<T> b, T one) {
+  return mk<T>(add1(a.x, b.x, one), add1(a.y, b.y, one));
+}
+template <typename T> __device__ __forceinline__ cplx<T> c_sub(cplx<T> a, cplx<T> b, T one) {
+  return mk<T>(sub1(a.x, b.x, one), sub1(a.y, b.y, one));
+}
 template <typename T> __device__ __forceinline__ cplx<T> c_mul(cplx<T> a, cplx<T> b) {
   return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -47,25 +63,25 @@ template <typename T, bool INV> __device__ __forceinline__ cplx<T> c_mi(cplx<T> 
 template <typename T, int R, bool INV> struct Dft;
 
 template <typename T, bool INV> struct Dft<T, 1, INV> {
-  __device__ __forceinline__ static void run(cplx<T>*) {}
+  __device__ __forceinline__ static void run(cplx<T>*, T) {}
 };
 
 template <typename T, bool INV> struct Dft<T, 2, INV> {
-  __device__ __forceinline__ static void run(cplx<T>* v) {
+  __device__ __forceinline__ static void run(cplx<T>* v, T one) {
     const cplx<T> a = v[0], b = v[1];
-    v[0] = c_add<T>(a, b);
-    v[1] = c_sub<T>(a, b);
+    v[0] = c_add<T>(a, b, one);
+    v[1] = c_sub<T>(a, b, one);
   }
 };
 
 template <typename T, bool INV> struct Dft<T, 4, INV> {
-  __device__ __forceinline__ static void run(cplx<T>* v) {
-    const cplx<T> s02 = c_add<T>(v[0], v[2]), d02 = c_sub<T>(v[0], v[2]);
-    const cplx<T> s13 = c_add<T>(v[1], v[3]), d13 = c_mi<T, INV>(c_sub<T>(v[1], v[3]));
-    v[0] = c_add<T>(s02, s13);
-    v[2] = c_sub<T>(s02, s13);
-    v[1] = c_add<T>(d02, d13);
-    v[3] = c_sub<T>(d02, d13);
+  __device__ __forceinline__ static void run(cplx<T>* v, T one) {
+    const cplx<T> s02 = c_add<T>(v[0], v[2], one), d02 = c_sub<T>(v[0], v[2], one);
+    const cplx<T> s13 = c_add<T>(v[1], v[3], one), d13 = c_mi<T, INV>(c_sub<T>(v[1], v[3], one));
+    v[0] = c_add<T>(s02, s13, one);
+    v[2] = c_sub<T>(s02, s13, one);
+    v[1] = c_add<T>(d02, d13, one);
+    v[3] = c_sub<T>(d02, d13, one);
   }
 };
 
@@ -73,39 +89,39 @@ template <typename T, bool INV> struct Dft<T, 4, INV> {
 // X[k] = E[k] + W^k O[k], X[k + H] = E[k] - W^k O[k], W = exp(-+ 2 pi i / 2H).
 // W^0 = 1 and W^(H/2) = -+i are applied without multiplications (same values up to
 // the sign of zero results).
-template <typename T, int H, bool INV> __device__ __forceinline__ void split2(cplx<T>* v, const cplx<T>* w) {
+template <typename T, int H, bool INV> __device__ __forceinline__ void split2(cplx<T>* v, const cplx<T>* w, T one) {
   cplx<T> e[H], o[H];
 #pragma unroll
   for (int k = 0; k < H; ++k) {
     e[k] = v[2 * k];
     o[k] = v[2 * k + 1];
   }
-  Dft<T, H, INV>::run(e);
-  Dft<T, H, INV>::run(o);
+  Dft<T, H, INV>::run(e, one);
+  Dft<T, H, INV>::run(o, one);
 #pragma unroll
   for (int k = 0; k < H; ++k) {
     const cplx<T> t = k == 0 ? o[k] : (2 * k == H ? c_mi<T, INV>(o[k]) : c_mul<T>(o[k], w[k]));
-    v[k] = c_add<T>(e[k], t);
-    v[k + H] = c_sub<T>(e[k], t);
+    v[k] = c_add<T>(e[k], t, one);
+    v[k + H] = c_sub<T>(e[k], t, one);
   }
 }
 
 template <typename T, bool INV> struct Dft<T, 8, INV> {
-  __device__ __forceinline__ static void run(cplx<T>* v) {
+  __device__ __forceinline__ static void run(cplx<T>* v, T one) {
     const T r = T(0.70710678118654752440);
     const T sg = INV ? T(1) : T(-1);
     const cplx<T> w[4] = {mk<T>(T(1), T(0)), mk<T>(r, sg * r), mk<T>(T(0), sg), mk<T>(-r, sg * r)};
-    split2<T, 4, INV>(v, w);
+    split2<T, 4, INV>(v, w, one);
   }
 };
 
 template <typename T, bool INV> struct Dft<T, 16, INV> {
-  __device__ __forceinline__ static void run(cplx<T>* v) {
+  __device__ __forceinline__ static void run(cplx<T>* v, T one) {
     const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), r = T(0.70710678118654752440);
     const T sg = INV ? T(1) : T(-1);
     const cplx<T> w[8] = {mk<T>(T(1), T(0)), mk<T>(c1, sg * s1), mk<T>(r, sg * r), mk<T>(s1, sg * c1),
                           mk<T>(T(0), sg),   mk<T>(-s1, sg * c1), mk<T>(-r, sg * r), mk<T>(-c1, sg * s1)};
-    split2<T, 8, INV>(v, w);
+    split2<T, 8, INV>(v, w, one);
   }
 };
 
@@ -114,7 +130,7 @@ template <typename T, bool INV> struct Dft<T, 16, INV> {
 // tw: twiddle table exp(-2 pi i m / (L tws)) in shared memory (read with plain loads).
 template <typename T, int RME, int R, bool INV, bool FROM_REGS>
 __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, cplx<T>* v, int j,
-                                          int TPL, int L, int Ns, const cplx<T>* __restrict__ tw, int tws) {
+                                          int TPL, int L, int Ns, const cplx<T>* __restrict__ tw, int tws, T one) {
   const int step = L / R;
 #pragma unroll
   for (int i = 0; i < RME / R; ++i) {
@@ -132,7 +148,7 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
         x[r] = c_mul<T>(x[r], w);
       }
     }
-    Dft<T, R, INV>::run(x);
+    Dft<T, R, INV>::run(x, one);
     const int base = (b - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[spad(base + r * Ns)] = x[r];
@@ -144,20 +160,20 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ src, cplx<
 // shared-memory buffers. Returns the buffer holding the natural-order result.
 template <typename T, int RM, bool INV>
 __device__ cplx<T>* line_fft(cplx<T>* v, int j, int L, cplx<T>* b0, cplx<T>* b1, const cplx<T>* __restrict__ tw,
-                             int tws) {
+                             int tws, T one) {
   cplx<T>* cur = b0;
   cplx<T>* nxt = b1;
   int Ns;
   if (L >= RM) {
     const int TPL = L / RM;
-    fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, TPL, L, 1, tw, tws);
+    fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, TPL, L, 1, tw, tws, one);
     Ns = RM;
   } else {
     // one lane holds the whole line (TPL = 1, j = 0)
     switch (L) {
-      case 2: fft_stage<T, 2, 2, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws); break;
-      case 4: fft_stage<T, 4, 4, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws); break;
-      case 8: fft_stage<T, 8, 8, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws); break;
+      case 2: fft_stage<T, 2, 2, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws, one); break;
+      case 4: fft_stage<T, 4, 4, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws, one); break;
+      case 8: fft_stage<T, 8, 8, INV, true>(nullptr, cur, v, j, 1, L, 1, tw, tws, one); break;
       default: break;
     }
     Ns = L;
@@ -167,13 +183,13 @@ __device__ cplx<T>* line_fft(cplx<T>* v, int j, int L, cplx<T>* b0, cplx<T>* b1,
   while (Ns < L) {
     const int rem = L / Ns;
     if (rem >= RM) {
-      fft_stage<T, RM, RM, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws);
+      fft_stage<T, RM, RM, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws, one);
       Ns *= RM;
     } else {
       switch (rem) {
-        case 2: fft_stage<T, RM, 2, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws); break;
-        case 4: fft_stage<T, RM, 4, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws); break;
-        case 8: fft_stage<T, RM, 8, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws); break;
+        case 2: fft_stage<T, RM, 2, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws, one); break;
+        case 4: fft_stage<T, RM, 4, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws, one); break;
+        case 8: fft_stage<T, RM, 8, INV, false>(cur, nxt, v, j, TPL, L, Ns, tw, tws, one); break;
         default: break;
       }
       Ns = L;
@@ -213,7 +229,7 @@ __device__ __forceinline__ void fill_stage_twiddles(cplx<T>* dst, const cplx<T>*
 
 template <typename T, int RM, int R, bool INV, int L, int NS>
 __device__ __forceinline__ void fft_stage_ct(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int j,
-                                             const cplx<T>* __restrict__ tst) {
+                                             const cplx<T>* __restrict__ tst, T one) {
   constexpr int TPL = L / RM;
   constexpr int step = L / R;
 #pragma unroll
@@ -229,7 +245,7 @@ __device__ __forceinline__ void fft_stage_ct(const cplx<T>* __restrict__ src, cp
       if (INV) w.y = -w.y;
       x[r] = c_mul<T>(x[r], w);
     }
-    Dft<T, R, INV>::run(x);
+    Dft<T, R, INV>::run(x, one);
     const int base = (b - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[spad(base + r * NS)] = x[r];
@@ -237,15 +253,16 @@ __device__ __forceinline__ void fft_stage_ct(const cplx<T>* __restrict__ src, cp
 }
 
 template <typename T, int RM, bool INV, int L, int NS>
-__device__ __forceinline__ void line_stages_ct(cplx<T>*& cur, cplx<T>*& nxt, int j, const cplx<T>* __restrict__ tst) {
+__device__ __forceinline__ void line_stages_ct(cplx<T>*& cur, cplx<T>*& nxt, int j, const cplx<T>* __restrict__ tst,
+                                               T one) {
   if constexpr (NS < L) {
     constexpr int R = StageRadix<RM, L, NS>::R;
-    fft_stage_ct<T, RM, R, INV, L, NS>(cur, nxt, j, tst);
+    fft_stage_ct<T, RM, R, INV, L, NS>(cur, nxt, j, tst, one);
     cplx<T>* t = cur;
     cur = nxt;
     nxt = t;
     __syncthreads();
-    line_stages_ct<T, RM, INV, L, NS * R>(cur, nxt, j, tst);
+    line_stages_ct<T, RM, INV, L, NS * R>(cur, nxt, j, tst, one);
   }
 }
 
@@ -253,13 +270,13 @@ __device__ __forceinline__ void line_stages_ct(cplx<T>*& cur, cplx<T>*& nxt, int
 // a barrier.
 template <typename T, int RM, bool INV, int L>
 __device__ __forceinline__ cplx<T>* line_fft_ct(cplx<T>* v, int j, cplx<T>* b0, cplx<T>* b1,
-                                                const cplx<T>* __restrict__ tst) {
+                                                const cplx<T>* __restrict__ tst, T one) {
   static_assert(L >= RM, "compile-time lines hold at least one radix-RM butterfly per lane");
   cplx<T>* cur = b0;
   cplx<T>* nxt = b1;
-  fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, L / RM, L, 1, nullptr, 1);
+  fft_stage<T, RM, RM, INV, true>(nullptr, cur, v, j, L / RM, L, 1, nullptr, 1, one);
   __syncthreads();
-  line_stages_ct<T, RM, INV, L, RM>(cur, nxt, j, tst);
+  line_stages_ct<T, RM, INV, L, RM>(cur, nxt, j, tst, one);
   return cur;
 }
 
