@@ -173,9 +173,10 @@ def traffic_bytes_per_unit(kernel, shape, d=2):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch with all three
 # loads active, from the ncu capture summarised in profiles/fp64_2d_1024_gj_kernels.md
-# (1024 x 1024, Green-Jacobi, contrast 1e4), for kernels unchanged since that capture
-# (empty: every kernel has changed since; their traffic stays null).
-NCU_TRAFFIC_PER_LAUNCH = {}
+# (1024 x 1024, Green-Jacobi, contrast 1e4), for kernels unchanged since that capture; the
+# FP32 kernels have no capture of all three loads active (their traffic stays null).
+NCU_TRAFFIC_PER_LAUNCH = {"fft_lines": 63.11e6 + 0.93e6, "apply_K": 59.86e6 + 11.20e6,
+                          "fft_cols_real_inv": 110.95e6 + 25.91e6, "fft_rows_real_fwd": 59.18e6 + 13.78e6}
 
 
 def aggregate(ms_local, world, solves_per_step, dist=None, device=None):
