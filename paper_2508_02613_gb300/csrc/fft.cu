@@ -8,8 +8,9 @@
 // contiguous lines, applies the d x d block of G_hat per frequency between the
 // forward and the inverse transform, and writes back in place; the inverse passes
 // mirror the forward ones. Every line FFT runs on the register-resident Stockham
-// engine of fft_engine.cuh (radix 16 in FP32, radix 8 in FP64, then one smaller
-// radix), twiddles from a per-axis table exp(-2 pi i m / n_a).
+// engine of fft_engine.cuh (radix 8, then one smaller radix), twiddles from a per-axis
+// table exp(-2 pi i m / n_a); line lengths 64 .. 2048 use the engine's compile-time
+// form with per-stage twiddle tables, other lengths the runtime form.
 //
 // Scaling: the real-axis forward post-pass omits its factor 1/2 and every inverse
 // pass is unnormalised, so the chain computes 2 N x the true F^-1 G F; the stored
