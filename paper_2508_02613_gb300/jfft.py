@@ -549,7 +549,7 @@ class Server:
         return {f: int(getattr(c, f)) for f, _ in JfftServerCounters._fields_}
 
 
-def workspace_estimate(shape, precision="fp64", max_loads=6) -> int:
+def workspace_estimate(shape, precision="fp64", max_loads=6, element="q1", material_bf16=False) -> int:
     """Device bytes jfft_create would allocate for this grid (jfft_workspace_estimate)."""
     lib = load()
     shape = tuple(int(v) for v in shape)
@@ -558,6 +558,8 @@ def workspace_estimate(shape, precision="fp64", max_loads=6) -> int:
     lib.jfft_default_options(ctypes.byref(opt))
     opt.precision = PRECISION[precision]
     opt.max_loads = max_loads
+    opt.element = ELEMENT[element]
+    opt.material_bf16 = 1 if material_bf16 else 0
     out = c_size_t()
     st = lib.jfft_workspace_estimate(ctypes.byref(g), ctypes.byref(opt), ctypes.byref(out))
     if st != JFFT_OK:

@@ -43,3 +43,15 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.jfft_apply_K(None, 1, None, None) == jfft.JFFT_ERR_ARG
     assert lib.jfft_launch_count(None) == 0
     assert lib.jfft_graph_replays(None) == 0
+
+
+def test_workspace_estimate_accounts_for_tables():
+    """Host-side sizing (no GPU): the BF16 material copy takes 2 bytes per voxel instead
+    of 4; the resolved J^1/2 table holds one factor per node for Q1 on a grid with equal
+    spacing and one per DOF for P1 voxels (FP64 table, plus its FP32 copy when mixed)."""
+    from paper_2508_02613_gb300.jfft import workspace_estimate
+    shape = (64, 64)
+    N = 64 * 64
+    assert workspace_estimate(shape, "mixed", 3) - workspace_estimate(shape, "mixed", 3, material_bf16=True) == 2 * N
+    assert workspace_estimate(shape, "fp64", 3, element="p1") - workspace_estimate(shape, "fp64", 3) == N * 8
+    assert workspace_estimate(shape, "mixed", 3, element="p1") - workspace_estimate(shape, "mixed", 3) == N * (8 + 4)
