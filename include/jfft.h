@@ -282,10 +282,16 @@ jfft_status jfft_postprocess(jfft_solver* h, int count, const double* eps_bar, c
  * so calls that may overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller.
  *
- * Errors: JFFT_ERR_ARG for NULL pointers, nu outside (-1, 0.5) or dim not 2/3;
- * JFFT_ERR_UNSUPPORTED for axis lengths that are not powers of two in 4..2048
- * (2D) / 4..1024 (3D) or a launch that would need more than 8192 partial sums;
- * JFFT_ERR_CUDA if a CUDA call fails.
+ * y must not overlap x or E (the kernel writes y while other blocks still read
+ * the halo layers of x), and xy must not overlap any of them: an in-place or
+ * overlapping call is refused with JFFT_ERR_ARG.
+ *
+ * Errors: JFFT_ERR_ARG for NULL or overlapping pointers, nu outside (-1, 0.5) or
+ * dim not 2/3; JFFT_ERR_UNSUPPORTED (nothing launched) for axis lengths that are
+ * not powers of two in 4..2048 (2D) / 4..1024 (3D) or a launch that would need
+ * more than 8192 partial sums; JFFT_ERR_CUDA if one of this call's own CUDA calls
+ * fails (an error left pending on the thread by earlier work is not read or
+ * cleared).
  */
 jfft_status jfft_apply_K_dot_noalloc(const jfft_grid* grid, double nu, const double* E, const double* x,
                                      double* y, double* xy, void* stream);

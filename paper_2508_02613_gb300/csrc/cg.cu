@@ -280,6 +280,19 @@ cudaError_t launch_reduce_partials(const double* partial, int nparts, int rows, 
   return cudaGetLastError();
 }
 
+// The same reduction for callers that must not read the thread's pending-error
+// slot: the status returned is the launch's own.
+cudaError_t launch_reduce_partials_own_status(const double* partial, int nparts, int rows, int64_t pstride,
+                                              double* out, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(rows);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaError_t e = cudaSuccess;
+  JFFT_K("reduce_rows", st, e = cudaLaunchKernelEx(&cfg, k_reduce_rows, partial, nparts, pstride, out));
+  return e;
+}
+
 // partial[row][blk] = sum of row `row` of x viewed as [rows][n]
 __global__ void __launch_bounds__(256) k_row_sums(const double* __restrict__ x, int64_t n, double* __restrict__ partial) {
   const int row = blockIdx.y;

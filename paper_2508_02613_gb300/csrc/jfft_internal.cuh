@@ -156,7 +156,9 @@ cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, 
                            double* y, int nb, int64_t field_stride, const StrainShift* shifts, double sgn, int dot_mode,
                            double* partial, int* nparts, CgState* cg, cudaStream_t st, StageCtl sc = no_stage());
 
-// S3, one rhs, with a caller-supplied partial buffer of `cap` entries (see operator.cu).
+// S3, one rhs, with a caller-supplied partial buffer of `cap` entries (see operator.cu);
+// nparts = -1 (nothing launched) if the launch would need more than `cap` partials.
+// Returns the launch's own status (cudaLaunchKernelEx), never a pending earlier error.
 cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const double* E, const double* x, double* y,
                                       double* partial, int cap, int* nparts, cudaStream_t st);
 
@@ -276,6 +278,10 @@ cudaError_t launch_gap(const Grid& g, const double* r64, const float* r32, int n
 // out[row] = sum_j partial[row * pstride + j] in a fixed order.
 cudaError_t launch_reduce_partials(const double* partial, int nparts, int rows, int64_t pstride, double* out,
                                    cudaStream_t st);
+// The same, returning the launch's own status (cudaLaunchKernelEx) without reading
+// or clearing an error left pending by earlier work.
+cudaError_t launch_reduce_partials_own_status(const double* partial, int nparts, int rows, int64_t pstride,
+                                              double* out, cudaStream_t st);
 // Row sums of x viewed as [rows][n] into partials; x[row][:] -= sums[row] / n.
 cudaError_t launch_row_sums(const double* x, int rows, int64_t n, double* partial, int* nparts, cudaStream_t st);
 cudaError_t launch_sub_mean(double* x, int rows, int64_t n, const double* sums, cudaStream_t st);

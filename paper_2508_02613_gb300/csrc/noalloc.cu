@@ -11,6 +11,7 @@
 #include "element.cuh"
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 namespace {
@@ -26,6 +27,12 @@ std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {};
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// True if the byte ranges [a, a + na) and [b, b + nb) share any byte.
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+  return pa < pb + nb && pb < pa + na;
+}
 
 }  // namespace
 
@@ -53,6 +60,15 @@ extern "C" jfft_status jfft_apply_K_dot_noalloc(const jfft_grid* grid, double nu
   }
   g.M = g.n[d - 1] / 2;
   g.F = g.N / g.n[d - 1] * (g.M + 1);
+  // y is written while neighbouring blocks still read x (halo layers) and E, and the
+  // kernel takes all three as non-aliasing: an in-place or overlapping call would be
+  // silently wrong, so it is refused.
+  const size_t field_bytes = sizeof(double) * (size_t)d * (size_t)g.N;
+  const size_t e_bytes = sizeof(double) * (size_t)g.N;
+  if (overlaps(y, field_bytes, x, field_bytes) || overlaps(y, field_bytes, E, e_bytes) ||
+      overlaps(xy, sizeof(double), y, field_bytes) || overlaps(xy, sizeof(double), x, field_bytes) ||
+      overlaps(xy, sizeof(double), E, e_bytes))
+    return JFFT_ERR_ARG;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return JFFT_ERR_CUDA;
@@ -73,13 +89,15 @@ extern "C" jfft_status jfft_apply_K_dot_noalloc(const jfft_grid* grid, double nu
   const double mu = 1.0 / (2.0 * (1.0 + nu));
   const ElemConst ec = make_elem_const(d, h, lam, mu);
   cudaStream_t st = (cudaStream_t)stream;
+  // Both launches report their own status; an error that earlier, unrelated work left
+  // pending on this thread is neither read nor cleared here.
   int nparts = 0;
   cudaError_t e = launch_apply_K_dot_capped(g, ec, E, x, y, partial, kNoAllocPartials, &nparts, st);
-  if (e == cudaErrorInvalidValue) return JFFT_ERR_UNSUPPORTED;  // needs more partial sums than the array holds
   if (e != cudaSuccess) return JFFT_ERR_CUDA;
+  if (nparts < 0) return JFFT_ERR_UNSUPPORTED;  // needs more partial sums than the array holds; nothing ran
   // Every slot the reduction reads was written by this call's operator launch, so
   // nothing in the shared array needs clearing first.
-  e = launch_reduce_partials(partial, nparts, 1, kMaxPartials, xy, st);
+  e = launch_reduce_partials_own_status(partial, nparts, 1, kMaxPartials, xy, st);
   if (e != cudaSuccess) return JFFT_ERR_CUDA;
   return JFFT_OK;
 }

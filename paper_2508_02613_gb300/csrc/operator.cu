@@ -583,25 +583,38 @@ cudaError_t launch_apply_K(const Grid& g, const ElemConst& ec, const double* E, 
 
 // The CG operator variant (y = K x with per-CTA partial sums of x.y) for a caller
 // that supplies its own partial-sum buffer with room for `cap` entries: the march
-// segment is lengthened until the CTA count fits (nparts receives that count), or
-// cudaErrorInvalidValue if even a full-length march needs more than `cap`.
+// segment is lengthened until the CTA count fits and nparts receives that count;
+// if even a full-length march needs more than `cap`, nparts receives -1 and nothing
+// is launched. The returned status is this call's own (cudaLaunchKernelEx reports
+// the launch's error directly, so an error left pending by earlier, unrelated work
+// is neither read nor cleared).
 template <int D>
 static cudaError_t apply_K_dot_capped_t(const Grid& g, const ElemConst& ec, const double* E, const double* x,
                                         double* y, double* partial, int cap, int* nparts, cudaStream_t st) {
   MarchGeom m = march_geom<D>(g);
   const int64_t tiles = (int64_t)m.tiles1 * m.tiles2;
   while (tiles * (g.n[0] / m.seg) > cap && m.seg < g.n[0]) m.seg *= 2;
-  if (tiles * (g.n[0] / m.seg) > cap) return cudaErrorInvalidValue;
+  if (tiles * (g.n[0] / m.seg) > cap) {
+    *nparts = -1;
+    return cudaSuccess;
+  }
   const size_t smem = march_smem<D>(m);
   auto kern = k_apply_K<double, D, 1, true, true, false>;
   cudaError_t e = allow_dynamic_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(m.tiles1 * m.tiles2, g.n[0] / m.seg, 1);
-  const int threads = ((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(m.tiles1 * m.tiles2, g.n[0] / m.seg, 1);
+  cfg.blockDim = dim3(((std::max(plane_elems<D>(m), m.P1 * m.P2) + 31) / 32) * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  const ElemConstT<double> ecd = ec;
+  const StrainShift* no_shift = nullptr;
+  CgState* no_cg = nullptr;
   JFFT_K("apply_K_dot_capped", st,
-         kern<<<grid, threads, smem, st>>>(g, m, ec, E, 0.0, x, y, 0, nullptr, 1.0, partial, nullptr, no_stage()));
-  *nparts = grid.x * grid.y;
-  return cudaGetLastError();
+         e = cudaLaunchKernelEx(&cfg, kern, g, m, ecd, E, 0.0, x, y, (int64_t)0, no_shift, 1.0, partial, no_cg,
+                                no_stage()));
+  *nparts = (int)(cfg.gridDim.x * cfg.gridDim.y);
+  return e;
 }
 
 cudaError_t launch_apply_K_dot_capped(const Grid& g, const ElemConst& ec, const double* E, const double* x, double* y,

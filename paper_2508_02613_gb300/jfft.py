@@ -168,11 +168,36 @@ def _f64(a, shape=None):
     return out
 
 
+def _check_noalloc_tensor(name, t, numel):
+    """The C call reads and writes raw device pointers with no way to check them, so the
+    binding requires contiguous float64 CUDA tensors on the current device, of the size
+    the grid implies, before it passes a pointer on."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch CUDA tensor, got {type(t).__name__}")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must live on the current CUDA device (cuda:{torch.cuda.current_device()}), "
+                         f"not {t.device}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, the grid needs {numel}")
+
+
 def apply_K_dot_noalloc(shape, nu, E, x, y, xy, stream=None) -> int:
     """jfft_apply_K_dot_noalloc on CUDA tensors E [*shape], x / y [d, *shape], xy [1];
-    returns the status code (no allocation happens in the library)."""
+    returns the status code (no allocation happens in the library). Raises ValueError
+    before the call if a tensor is not a contiguous float64 tensor on the current
+    CUDA device with the element count the grid implies."""
     lib = load()
     d = len(shape)
+    N = int(np.prod([int(v) for v in shape]))
+    _check_noalloc_tensor("E", E, N)
+    _check_noalloc_tensor("x", x, d * N)
+    _check_noalloc_tensor("y", y, d * N)
+    _check_noalloc_tensor("xy", xy, 1)
     g = JfftGrid(d, (c_int64 * 3)(*(list(int(s) for s in shape) + [0] * (3 - d))))
     return lib.jfft_apply_K_dot_noalloc(ctypes.byref(g), float(nu), _ptr(E), _ptr(x), _ptr(y), _ptr(xy),
                                         c_void_p(stream) if stream else None)

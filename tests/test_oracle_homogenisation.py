@@ -85,3 +85,10 @@ def test_hill_bounds_symmetry_and_energy(shape):
     # strict improvement over both bounds for a non-uniform field
     assert np.linalg.eigvalsh(voigt - Ch).max() > 1e-6 * scale
     assert out.rel_res.max() < 1e-11
+    # energy: eps_bar . C_hom eps_bar = <(eps_bar + B u) . E C (eps_bar + B u)>, which at
+    # the solution of K u = f is eps_bar^T C_Voigt eps_bar - f . u
+    from oracle import assemble
+    for g, eps in enumerate(mandel_unit_loads(d)):
+        f = assemble.assemble_rhs(shape, E, prob.C, eps)
+        energy = eps @ voigt @ eps - float(np.sum(f * out.u[g]))
+        assert abs(Ch[g, g] - energy) <= 1e-10 * abs(energy)
