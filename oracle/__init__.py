@@ -25,8 +25,10 @@ Pins (checked by ``tests/test_oracle_*.py``, run with ``-m "not gpu"``): textboo
 Q1 element entries, symmetry / semidefiniteness / rigid-translation kernel of K,
 Alg. 1 equal to a hand-derived closed-form symbol and to an explicit DFT, Alg. 2
 equal to the assembled diagonal, one-iteration convergence on homogeneous
-material, dense brute force, the laminate closed form, Hill bounds, and the
-paper's printed material constants. Exact PCG iteration counts at the benchmark
+material, dense brute force, the laminate closed form, Hill bounds, the energy
+identity, element stresses against a nodal-difference brute force and against the
+laminate's constant normal stress, the node-by-node operator against the assembled
+one, and the paper's printed material constants. Exact PCG iteration counts at the benchmark
 workloads have no printed value in the paper: parity unpinned for those counts
 (they are compared GPU-vs-oracle only).
 """
