@@ -68,3 +68,33 @@ def assemble_rhs(n, E: np.ndarray, C: np.ndarray, eps_bar: np.ndarray, element: 
 def apply(K: sp.csr_matrix, u: np.ndarray) -> np.ndarray:
     """K u for a field u of shape [d, *n]."""
     return (K @ u.reshape(-1)).reshape(u.shape)
+
+
+def apply_matrix_free(n, E: np.ndarray, C: np.ndarray, u: np.ndarray, element: str = "q1") -> np.ndarray:
+    """K u = B^T W C(rho) B u evaluated element by element (the matrix-free product of
+    Sec. 3.1), for a field u of shape [d, *n].
+
+    For every element e: the nodal values of its corners minus the value at its corner 0
+    (A = sum_q w_q B_q^T C B_q annihilates a constant field, so A u_e = A (u_e - u_e[0])
+    exactly), the element forces E_e A (u_e - u_e[0]), added into the nodes corner by
+    corner. Equal to ``apply(assemble_K(...), u)`` in exact arithmetic; on smooth fields
+    it keeps the relative accuracy that the assembled product loses by summing large
+    entries of alternating sign (about eps (n / 2 pi)^2 at the lowest frequency),
+    because the differences of neighbouring values are formed first."""
+    n = tuple(int(k) for k in n)
+    d = len(n)
+    axes = tuple(range(1, d + 1))
+    cs = fe.corners(d)
+    nc = len(cs)
+    N = int(np.prod(n))
+    A = fe.element_matrix(d, grid_spacing(n), C, element)
+    # ue[e, alpha * nc + c] = u[alpha][e + o_c] - u[alpha][e]
+    ue = np.stack([np.roll(u, tuple(-o for o in oc), axes) for oc in cs], axis=-1)  # [d, *n, nc]
+    ue = ue - ue[..., :1]
+    ue = np.moveaxis(ue.reshape(d, N, nc), 1, 0).reshape(N, d * nc)
+    Ef = np.asarray(E).reshape(-1)
+    forces = (Ef[:, None] * (ue @ A.T)).reshape(N, d, nc)
+    q = np.zeros((d,) + n, dtype=forces.dtype)
+    for ci, oc in enumerate(cs):
+        q += np.roll(np.moveaxis(forces[:, :, ci], 0, 1).reshape((d,) + n), tuple(oc), axes)
+    return q

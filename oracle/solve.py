@@ -1,7 +1,8 @@
 """The whole cell-problem solve, step by step (paper Secs. 2-4).
 
 For each macroscopic load eps_bar_gamma (Mandel vector):
-  1. assemble K(rho) and f_gamma = -B^T W C(rho) eps_bar_gamma  (Eq. lin_system_exp);
+  1. K(rho) (applied matrix-free, B^T W C B element by element, or assembled) and
+     f_gamma = -B^T W C(rho) eps_bar_gamma  (Eq. lin_system_exp);
   2. build the preconditioner: Green F^-1 G_hat F (Alg. 1, C_ref = mean(E) C_unit(nu)
      unless given), Jacobi diag(K)^-1 with the void rule, or Green-Jacobi
      J^(1/2) F^-1 G_hat F J^(1/2) (Eq. prec_lin_systemJG_2);
@@ -37,12 +38,15 @@ class CellProblem:
     diag: np.ndarray
     J_half: np.ndarray
     element: str = "q1"
+    operator: str = "matrix_free"
 
     @property
     def d(self):
         return len(self.n)
 
     def apply_K(self, u):
+        if self.operator == "matrix_free":
+            return assemble.apply_matrix_free(self.n, self.E, self.C, u, self.element)
         return assemble.apply(self.K, u)
 
     def minv(self, precond: str):
@@ -58,9 +62,29 @@ class CellProblem:
 
 
 def setup(n, E: np.ndarray, nu: float, C_ref: np.ndarray | None = None,
-          void_replacement: float = 1.0, element: str = "q1") -> CellProblem:
+          void_replacement: float = 1.0, element: str = "q1", operator: str = "matrix_free",
+          symbol: str = "support", precision: str = "fp64") -> CellProblem:
     """``element``: "q1" (bilinear / trilinear voxels, full Gauss rule) or "p1" (2D: each
-    voxel split into two linear triangles, fe.triangle_pair_B)."""
+    voxel split into two linear triangles, fe.triangle_pair_B).
+
+    ``operator``: how PCG applies K. "matrix_free" (default) evaluates B^T W C B element
+    by element on corner differences (assemble.apply_matrix_free, the matrix-free
+    product of Sec. 3.1); "assembled" multiplies by the sparse matrix. Both are K; they
+    differ only in rounding, which on the smooth fields of long solves is ~eps/theta for
+    the first and ~eps/theta^2 for the second (theta the lowest grid frequency).
+    ``symbol``: how step 2 of Alg. 1 transforms the impulse responses, "support"
+    (default, green.support_transform) or "fft" (the full FFT, real and even part).
+    ``precision``: "fp64", or "extended" (numpy.longdouble, 64-bit significand on x86)
+    for the matrix-free operator, the symbol, J^(1/2) and every PCG vector and scalar
+    (the inputs E, C and the diagonal are the FP64 values); it measures how far FP64
+    rounding moves the PCG iteration counts."""
+    if operator not in ("matrix_free", "assembled"):
+        raise ValueError(operator)
+    if precision not in ("fp64", "extended"):
+        raise ValueError(precision)
+    if precision == "extended" and (operator != "matrix_free" or symbol != "support"):
+        raise ValueError("extended precision needs the matrix-free operator and the support-form symbol")
+    dt = np.longdouble if precision == "extended" else np.float64
     n = tuple(int(k) for k in n)
     d = len(n)
     E = np.asarray(E, dtype=np.float64).reshape(n)
@@ -68,10 +92,12 @@ def setup(n, E: np.ndarray, nu: float, C_ref: np.ndarray | None = None,
     K = assemble.assemble_K(n, E, C, element)
     if C_ref is None:
         C_ref = float(E.mean()) * C
-    _, G_hat = green.green_symbol(n, C_ref, element=element)
+    _, G_hat = green.green_symbol(n, C_ref, element=element, transform=symbol, dtype=dt)
     diag = jacobi.diag_assembled(K, (d,) + n)
     J_half = jacobi.jacobi_half(diag, void_replacement)
-    return CellProblem(n, E, nu, C, K, G_hat, diag, J_half, element)
+    if dt is not np.float64:
+        E, C, J_half = E.astype(dt), C.astype(dt), J_half.astype(dt)
+    return CellProblem(n, E, nu, C, K, G_hat, diag, J_half, element, operator)
 
 
 @dataclass
@@ -94,7 +120,7 @@ def solve(prob: CellProblem, eps_bar: np.ndarray, tol: float, precond: str,
     us, raws, stresses, chom, its, rres = [], [], [], [], [], []
     minv = prob.minv(precond)
     for g in range(nl):
-        f = assemble.assemble_rhs(prob.n, prob.E, prob.C, eps_bar[g], prob.element)
+        f = assemble.assemble_rhs(prob.n, prob.E, prob.C, eps_bar[g], prob.element).astype(prob.E.dtype)
         if fixed_iters is not None:
             res = pcg.pcg(prob.apply_K, minv, f, 0.0, int(fixed_iters[g]), "rel", dot_order)
         else:

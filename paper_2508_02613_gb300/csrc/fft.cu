@@ -1,5 +1,5 @@
-// FP64 instances of the Green / Green-Jacobi preconditioner passes (fft_passes.cuh),
-// the forward transform of Alg. 1 (S9) and the twiddle tables.
+// FP64 instances of the Green / Green-Jacobi preconditioner passes (fft_passes.cuh)
+// and the twiddle tables.
 #include "fft_passes.cuh"
 
 namespace jfft {
@@ -21,16 +21,6 @@ cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* 
                                  int64_t /*field_stride*/, const double* js, bool jacobi, double* partial, int* nparts,
                                  CgState* done, cudaStream_t st, StageCtl sc, int64_t jcs) {
   return green_precond_t<double>(g, p, r, z, nb, js, jacobi, partial, nparts, done, st, sc, jcs);
-}
-
-cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
-                                    const double2** spec_out, cudaStream_t st) {
-  JScaleT<double> jsc = {};
-  JFFT_TRY(pass_rows_real_fwd<double>(g, p, r, nb, false, nullptr, jsc, nullptr, st));
-  if (g.d == 3) JFFT_TRY(pass_rows_cplx_fwd<double>(g, p, nb, nullptr, st));
-  JFFT_TRY(pass_lines<double>(g, p, nb, false, nullptr, st));
-  *spec_out = (g.d == 2) ? p.T : p.U;
-  return cudaSuccess;
 }
 
 }  // namespace jfft

@@ -319,16 +319,14 @@ static jfft_status validate_material(jfft_solver* h, const jfft_material* m, int
   return JFFT_OK;
 }
 
-// Alg. 1 on the device: impulse responses of K_ref, forward transform, inversion.
+// Alg. 1 on the device: impulse responses of K_ref, their transform (evaluated over
+// the responses' 3^d-node support, free of low-frequency cancellation), inversion.
 static jfft_status build_symbol(jfft_solver* h) {
   const Grid& g = h->g;
   CK(launch_impulses(g, h->x, h->st));
   CK(launch_apply_K(g, h->ec_ref, nullptr, 1.0, h->x, h->z, g.d, field_elems(h), nullptr, 1.0, 0, nullptr, nullptr,
                     nullptr, h->st));
-  FftPlan pl = {{h->tw[0], h->tw[1], h->tw[2]}, h->T, h->U, h->G};
-  const double2* spec = nullptr;
-  CK(launch_forward_spectrum(g, pl, h->z, g.d, &spec, h->st));
-  CK(launch_green_table(g, spec, h->G, h->scale_store, h->st));
+  CK(launch_green_table(g, h->z, field_elems(h), h->G, h->scale_store, h->st));
   return JFFT_OK;
 }
 

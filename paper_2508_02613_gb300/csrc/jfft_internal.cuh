@@ -195,7 +195,11 @@ cudaError_t launch_fill_comb(const Grid& g, int comp, int offbits, double* x, cu
 cudaError_t launch_extract_comb(const Grid& g, int comp, int offbits, const double* y, double* diag, cudaStream_t st);
 // S9 (Alg. 1): d unit-impulse fields [d][d][N]; block inversion into the table.
 cudaError_t launch_impulses(const Grid& g, double* x, cudaStream_t st);
-cudaError_t launch_green_table(const Grid& g, const double2* spec, double* G, double scale_store, cudaStream_t st);
+// Steps 2-3 of Alg. 1 from the impulse responses R [d][fstride] (field alpha = the
+// response to the unit impulse in component alpha at node 0; component beta at
+// offset beta * N): transform over the 3^d-node support, inversion, table of G_hat.
+cudaError_t launch_green_table(const Grid& g, const double* R, int64_t fstride, double* G, double scale_store,
+                               cudaStream_t st);
 cudaError_t launch_green_export(const Grid& g, const double* G, double* out, double scale_store, cudaStream_t st);
 
 // S6: twiddle table exp(-2 pi i m / n), m < n.
@@ -218,9 +222,6 @@ cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* 
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
                                      const float* js, bool jacobi, double* partial, int* nparts, CgState* cg,
                                      cudaStream_t st, StageCtl sc = no_stage(), int64_t jcs = 0);
-// Forward transform of nb d-component real fields -> line-major spectrum [nb][d][F].
-cudaError_t launch_forward_spectrum(const Grid& g, const FftPlan& p, const double* r, int nb,
-                                    const double2** spec_out, cudaStream_t st);
 // z = J r (J = diag(K)^-1 with the void rule) or z = r (identity), partial r.z.
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
                                   bool identity, double* partial, int* nparts, CgState* cg, cudaStream_t st,

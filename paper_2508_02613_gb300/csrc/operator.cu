@@ -899,24 +899,77 @@ cudaError_t launch_impulses(const Grid& g, double* x, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Step 3 of Alg. 1: invert the d x d block at every stored frequency; zero frequency
-// set to 0. spec holds our forward transform (2 x the unnormalised DFT) of the
-// responses R[alpha][beta]; the table stores G_hat * scale_store, upper triangle
-// in the order (00, 01, 11) / (00, 01, 02, 11, 12, 22).
+// Steps 2-3 of Alg. 1 at every stored frequency of the half spectrum (k_0 fastest, the
+// last axis halved): the transform of the impulse responses R[alpha][beta] of K_ref,
+// then the d x d inversion, the zero frequency set to 0; the table stores
+// G_hat * scale_store, upper triangle in the order (00, 01, 11) / (00, 01, 02, 11, 12, 22).
+//
+// Step 2 is evaluated over the support of R, the 3^D nodes that share an element with
+// node 0 (offsets J in {-1, 0, 1}^D). Each R[alpha][beta] sums to zero (K_ref maps a
+// rigid translation to zero), so its transform, the cosine sum over J, equals
+//   K_hat(k) = -2 sum_J R(J) sin^2(pi k.J / n),
+// in which every term keeps full relative accuracy at the lowest frequencies, where the
+// full FFT of R would lose ~eps (n / 2 pi)^2 to cancellation. The phase k.J / n is an
+// exact dyadic number; it is reduced to [-1/2, 1/2] exactly before sinpi. J and -J
+// share one phase, so each pair is evaluated once with the sum R(J) + R(-J).
 template <int D>
-__global__ void k_green_table(Grid g, const double2* __restrict__ spec, double* __restrict__ G, double scale_store) {
+__global__ void __launch_bounds__(256) k_green_table(Grid g, const double* __restrict__ R, int64_t fstride,
+                                                     double* __restrict__ G, double scale_store) {
+  constexpr int NJ = D == 2 ? 9 : 27;   // offsets J in {-1, 0, 1}^D, J_0 slowest
+  constexpr int NP = (NJ - 1) / 2;      // pairs {J, -J} with J != 0
   constexpr int NCMP = D * (D + 1) / 2;
+  __shared__ double cp[NP][D][D];       // R(J) + R(-J) of the pair's first member J
+  __shared__ int jof[NP][D];
+  for (int t = threadIdx.x; t < NP * D * D; t += blockDim.x) {
+    const int p = t / (D * D), a = (t / D) % D, b = t % D;
+    // pair p: offset index p + NP + 1 (above the centre NP) and its mirror -J
+    int rem = p + NP + 1;
+    int off[D];
+#pragma unroll
+    for (int c = D - 1; c >= 0; --c) { off[c] = rem % 3 - 1; rem /= 3; }
+    int64_t node_p = 0, node_m = 0;  // flat node index of J and of -J (periodic)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      node_p = node_p * g.n[c] + (off[c] + g.n[c]) % g.n[c];
+      node_m = node_m * g.n[c] + (g.n[c] - off[c]) % g.n[c];
+    }
+    const double* Rab = R + (int64_t)a * fstride + (int64_t)b * g.N;
+    cp[p][a][b] = Rab[node_p] + Rab[node_m];
+    if (a == 0 && b == 0) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) jof[p][c] = off[c];
+    }
+  }
+  __syncthreads();
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < g.F; f += (int64_t)gridDim.x * blockDim.x) {
+    int k[D];
+    int64_t rem = f;
+#pragma unroll
+    for (int c = 0; c < D - 1; ++c) { k[c] = (int)(rem % g.n[c]); rem /= g.n[c]; }
+    k[D - 1] = (int)rem;
     double K[D][D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = 0; b < D; ++b) K[a][b] = 0.5 * spec[((int64_t)a * D + b) * g.F + f].x;
+      for (int b = 0; b < D; ++b) K[a][b] = 0.0;
+#pragma unroll 1
+    for (int p = 0; p < NP; ++p) {
+      double ph = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) ph += (double)(k[c] * jof[p][c]) / (double)g.n[c];
+      ph -= rint(ph);
+      const double sn = sinpi(ph);
+      const double s2 = -2.0 * sn * sn;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) K[a][b] = fma(cp[p][a][b], s2, K[a][b]);
+    }
     // symmetrise (the symbol is real symmetric; this removes rounding asymmetry)
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = a + 1; b < D; ++b) { const double s = 0.5 * (K[a][b] + K[b][a]); K[a][b] = K[b][a] = s; }
+      for (int b = a + 1; b < D; ++b) { const double sy = 0.5 * (K[a][b] + K[b][a]); K[a][b] = K[b][a] = sy; }
     double out[NCMP];
     if (f == 0) {
 #pragma unroll
@@ -942,10 +995,11 @@ __global__ void k_green_table(Grid g, const double2* __restrict__ spec, double* 
   }
 }
 
-cudaError_t launch_green_table(const Grid& g, const double2* spec, double* G, double scale_store, cudaStream_t st) {
+cudaError_t launch_green_table(const Grid& g, const double* R, int64_t fstride, double* G, double scale_store,
+                               cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>((g.F + 255) / 256, 152 * 16);
-  if (g.d == 2) JFFT_K("green_table", st, k_green_table<2><<<blocks, 256, 0, st>>>(g, spec, G, scale_store));
-  else JFFT_K("green_table", st, k_green_table<3><<<blocks, 256, 0, st>>>(g, spec, G, scale_store));
+  if (g.d == 2) JFFT_K("green_table", st, k_green_table<2><<<blocks, 256, 0, st>>>(g, R, fstride, G, scale_store));
+  else JFFT_K("green_table", st, k_green_table<3><<<blocks, 256, 0, st>>>(g, R, fstride, G, scale_store));
   return cudaGetLastError();
 }
 

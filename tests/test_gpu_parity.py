@@ -48,7 +48,8 @@ def rel(a, b):
 SHAPES = [(4, 4), (8, 16), (16, 8), (64, 512), (4, 4, 4), (8, 4, 16), (16, 16, 64)]
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + [(1024, 64), (64, 1024), (2048, 16), (16, 2048), (8, 128, 8),
+                                            (128, 8, 16), (8, 8, 1024)])
 def test_material_and_operator(shape):
     d = len(shape)
     rho, E = _problem(shape, 1)
@@ -59,6 +60,26 @@ def test_material_and_operator(shape):
     y = s.apply_K(x)
     want = np.stack([assemble.apply(K, x[i]) for i in range(2)])
     assert rel(y, want) <= 1e-13
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024), (2048, 2048), (128, 128, 128), (512, 64, 64)])
+def test_operator_sampled_nodes_full_size(shape):
+    """At full size, K x on 4096 sampled nodes (every grid edge and corner among them)
+    against the oracle's node-by-node evaluation (no assembly)."""
+    from oracle import pointwise
+    d = len(shape)
+    rho, E = _problem(shape, 2)
+    s = _solver(shape, rho, max_loads=d)
+    x = random_field((1, d) + shape, 8)
+    y = s.apply_K(x)[0]
+    rng = np.random.default_rng(len(shape))
+    N = int(np.prod(shape))
+    edge = [np.ravel_multi_index(tuple(c), shape) for c in np.ndindex(*([2] * d))]
+    edge += [np.ravel_multi_index(tuple(m - 1 - c for m, c in zip(shape, cc)), shape) for cc in np.ndindex(*([2] * d))]
+    nodes = np.unique(np.concatenate([rng.choice(N, 4096, replace=False), edge]))
+    want = pointwise.apply_K_at(shape, E, fe.C_unit(d, 0.3), x[0], nodes)
+    got = y.reshape(d, -1)[:, nodes].T
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -94,27 +115,63 @@ def _half_spectrum(G_hat, shape):
     return np.transpose(g, axes).reshape(-1, d, d)
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (16, 4), (4, 8, 16), (8, 8, 8)])
+# Every compile-time FFT line length (64..2048) on each transformed axis: the real axis
+# (last), the axis-0 pass, and in 3D the middle axis; plus the small and ragged grids.
+FFT_SHAPES = [(4, 4), (8, 16), (16, 8), (64, 512), (1024, 64), (64, 1024), (2048, 16), (16, 2048), (128, 256),
+              (1024, 1024), (4, 4, 4), (8, 4, 16), (16, 16, 64), (8, 8, 1024), (8, 128, 8), (128, 8, 16),
+              (256, 4, 8), (4, 2048 // 4, 8), (8, 8, 256)]
+
+def alg1_tol(shape, base):
+    """Symbol tables are compared block by block, ||G_gpu(k) - G_ref(k)|| <= tol ||G_ref(k)||
+    at every stored frequency k != 0. Both sides evaluate step 2 of Alg. 1 over the
+    impulse responses' support, every term to a few ulps: on square / cubic grids a few
+    ulps per block remain (``base``). On elements with sides h_a = 1/n_a the long-side
+    couplings of the responses are O(h_max/h_min) and their sums over one offset are
+    O(h_min/h_max), so the FP64 rounding of the responses limits either side to
+    ~eps (h_max/h_min)^2 relative at the low frequencies across the short side (the
+    oracle's own table is that far from the closed form; tests/test_oracle_operator.py)."""
+    ratio = max(shape) / min(shape)
+    return max(base, 8 * np.finfo(np.float64).eps * ratio ** 2)
+
+
+def _block_rel(a, b):
+    """Largest block-relative difference over the frequencies (blocks [F, d, d]), k = 0 skipped
+    (both sides pin it to zero; checked separately)."""
+    na = np.linalg.norm(a[1:] - b[1:], axis=(1, 2))
+    nb = np.linalg.norm(b[1:], axis=(1, 2))
+    return float((na / nb).max())
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (16, 4), (4, 8, 16), (8, 8, 8), (1024, 1024), (2048, 16), (16, 2048),
+                                   (8, 8, 1024), (128, 8, 16)])
 def test_green_symbol_alg1(shape):
     d = len(shape)
     rho, E = _problem(shape, 4)
     s = _solver(shape, rho)
     _, G_hat = green.green_symbol(shape, E.mean() * fe.C_unit(d, 0.3))
-    assert rel(s.get_green(), _half_spectrum(G_hat, shape)) <= symbol_tol(shape)
+    got = s.get_green()
+    want = _half_spectrum(G_hat, shape)
+    assert np.abs(got[0]).max() == 0.0
+    assert _block_rel(got, want) <= alg1_tol(shape, 1e-14)
 
 
-def symbol_tol(shape):
-    """Alg. 1 obtains K_hat by transforming impulse responses whose O(1) entries cancel to
-    O(theta^2) at the lowest frequency theta_min = 2 pi / n_max, so each side's symbol
-    carries a relative rounding error of order eps (n_max / 2 pi)^2 there, and the Green
-    operator's output is dominated by those frequencies."""
-    eps = np.finfo(np.float64).eps
-    return max(1e-13, 20 * eps * (max(shape) / (2 * np.pi)) ** 2)
+@pytest.mark.parametrize("shape", [(1024, 1024), (128, 128, 128), (2048, 16), (8, 8, 1024), (64, 512)])
+def test_green_symbol_against_closed_form(shape):
+    """The table against the plane-wave closed form of the uniform Q1 operator, derived from
+    the element and not from impulse responses."""
+    d = len(shape)
+    rho, E = _problem(shape, 4)
+    s = _solver(shape, rho)
+    _, G_cf = green.closed_form_symbol(shape, E.mean() * fe.C_unit(d, 0.3))
+    assert _block_rel(s.get_green(), _half_spectrum(G_cf, shape)) <= alg1_tol(shape, 1e-14)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", FFT_SHAPES)
 @pytest.mark.parametrize("pc", ["green", "green_jacobi", "jacobi"])
 def test_preconditioners(shape, pc):
+    """Element by element against the oracle (numpy FFT, support-form symbol): the two
+    transforms round differently, ~eps log2 N relative to the output's scale; on stretched
+    grids the symbols' own limit (alg1_tol) dominates."""
     d = len(shape)
     rho, E = _problem(shape, 5)
     s = _solver(shape, rho)
@@ -123,7 +180,7 @@ def test_preconditioners(shape, pc):
     z = s.apply_precond(pc, r)
     minv = prob.minv(pc)
     want = np.stack([minv(r[i]) for i in range(2)])
-    assert rel(z, want) <= (symbol_tol(shape) if pc != "jacobi" else 1e-15)
+    assert rel(z, want) <= (alg1_tol(shape, 1e-13) if pc != "jacobi" else 1e-15)
 
 
 @pytest.mark.parametrize("shape", [(16, 16), (8, 8, 8)])

@@ -144,18 +144,20 @@ def test_preconditioners_are_symmetric(pc):
     assert abs(np.vdot(a, Mb) - np.vdot(b, Ma)) <= 1e-15 * np.linalg.norm(a) * np.linalg.norm(Mb) * 16
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (32, 32), (4, 4, 4), (8, 8, 8)])
+@pytest.mark.parametrize("shape", [(8, 8), (32, 32), (4, 4, 4), (8, 8, 8), (4, 8), (16, 4), (4, 8, 16), (8, 4, 4)])
 def test_closed_form_symbol_equals_alg1(shape):
-    """The oracle's plane-wave closed form (used to bracket iteration counts) equals
-    Alg. 1 and the hand-derived formula of this file."""
+    """The oracle's plane-wave closed form (rectangular elements h_a = 1/n_a) equals Alg. 1
+    with the explicit DFT of the assembled operator's impulse responses, and, on square /
+    cubic grids, the hand-derived formula of this file."""
     d = len(shape)
     C = 0.8 * fe.C_unit(d, 0.3)
-    K1, G1 = green.green_symbol(shape, C)
+    K1, G1 = green.green_symbol(shape, C, explicit_dft=True)
     K2, G2 = green.closed_form_symbol(shape, C)
     assert np.abs(K1 - K2).max() <= 1e-13 * np.abs(K1).max()
     assert np.abs(G1 - G2).max() <= 1e-12 * np.abs(G1).max()
-    lam, mu = float(C[0, 1]), 0.5 * float(C[0, 0] - C[0, 1])
-    assert np.abs(K2 - _closed_form_symbol(shape, lam, mu)).max() <= 1e-13 * np.abs(K2).max()
+    if len(set(shape)) == 1:
+        lam, mu = float(C[0, 1]), 0.5 * float(C[0, 0] - C[0, 1])
+        assert np.abs(K2 - _closed_form_symbol(shape, lam, mu)).max() <= 1e-13 * np.abs(K2).max()
 
 
 def test_library_fft_equals_explicit_dft():
@@ -233,3 +235,95 @@ def test_void_rule():
     assert np.all(jacobi.void_rule(dg)[:, 3:5, 3:5] == 1.0)
     jh = jacobi.jacobi_half(dg)
     assert np.all(np.isfinite(jh)) and np.all(jh[:, 3:5, 3:5] == 1.0)
+
+
+# ---- Alg. 1 step 2 over the impulse responses' support, and the matrix-free operator
+
+
+@pytest.mark.parametrize("shape,element", [((4, 4), "q1"), ((8, 4), "q1"), ((4, 8, 4), "q1"), ((8, 8), "p1"),
+                                           ((4, 16), "p1")])
+def test_support_transform_equals_explicit_dft(shape, element):
+    """The support form of step 2 is the DFT of the impulse responses: equal to the explicit
+    O(N^2) DFT (real, even part); the responses live on the 3^d nodes next to node 0."""
+    d = len(shape)
+    C = 0.9 * fe.C_unit(d, 0.28)
+    R = green.impulse_responses(shape, C, element)
+    far = np.ones(shape, dtype=bool)
+    far[np.ix_(*[[0, 1, m - 1] for m in shape])] = False
+    assert np.abs(R[..., far]).max() == 0.0
+    K1, G1 = green.green_symbol(shape, C, element=element)
+    K2, G2 = green.green_symbol(shape, C, explicit_dft=True, element=element)
+    assert np.abs(K1 - K2).max() <= 1e-14 * np.abs(K2).max()
+    assert np.abs(G1 - G2).max() <= 1e-13 * np.abs(G2).max()
+
+
+def alg1_block_tol(shape, base=1e-14):
+    """Block-relative accuracy of Alg. 1 evaluated from FP64 impulse responses. On elements
+    with sides h_a = 1/n_a, the couplings along the long side are O(h_max/h_min) while
+    their sums over one offset (which the low frequencies across the short side see) are
+    O(h_min/h_max): the FP64 rounding of the responses alone then limits any evaluation
+    of step 2 to ~eps (h_max/h_min)^2 relative there. Square / cubic grids: ``base``."""
+    ratio = max(shape) / min(shape)
+    return max(base, 8 * np.finfo(np.float64).eps * ratio ** 2)
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024), (2048, 2048), (128, 128, 128), (2048, 16), (8, 8, 1024),
+                                   (128, 8, 16), (1024, 64)])
+def test_support_transform_is_accurate_at_low_frequencies(shape):
+    """Block by block, the support-form symbol equals the plane-wave closed form (derived
+    from the element, not from the impulse responses) to a few ulps at every frequency,
+    the lowest included, on square / cubic grids, and to the responses' own FP64 limit
+    on stretched grids; the full FFT of the responses does not (cancellation of O(1)
+    entries down to O(theta^2), a relative error ~eps (n / 2 pi)^2)."""
+    d = len(shape)
+    C = 0.37 * fe.C_unit(d, 0.3)
+    Ks, Gs = green.green_symbol(shape, C)
+    Kc, Gc = green.closed_form_symbol(shape, C)
+    blocks = lambda X: np.moveaxis(X.reshape(d, d, -1), 2, 0)[1:]  # noqa: E731
+    for X, Y in ((Ks, Kc), (Gs, Gc)):
+        bx, by = blocks(X), blocks(Y)
+        err = np.linalg.norm(bx - by, axis=(1, 2)) / np.linalg.norm(by, axis=(1, 2))
+        assert err.max() <= alg1_block_tol(shape)
+    if len(set(shape)) > 1:
+        return
+    if d == 2:
+        _, Gf = green.green_symbol(shape, C, transform="fft")
+        bf, bc = blocks(Gf), blocks(Gc)
+        err_fft = np.linalg.norm(bf - bc, axis=(1, 2)) / np.linalg.norm(bc, axis=(1, 2))
+        assert err_fft.max() > 1e-12
+
+
+@pytest.mark.parametrize("shape,element", [((4, 8), "q1"), ((8, 4, 4), "q1"), ((4, 4, 2), "q1"), ((8, 16), "p1")])
+def test_matrix_free_operator_equals_assembled(shape, element):
+    d = len(shape)
+    rng = np.random.default_rng(3)
+    E = rng.uniform(0.05, 1.0, shape)
+    C = fe.C_unit(d, 0.3)
+    x = random_field((d,) + shape, 9)
+    K = assemble.assemble_K(shape, E, C, element)
+    want = assemble.apply(K, x)
+    got = assemble.apply_matrix_free(shape, E, C, x, element)
+    assert np.abs(got - want).max() <= 1e-14 * np.abs(want).max()
+    for a in range(d):  # a rigid translation gives exactly zero (corner differences vanish)
+        t = np.zeros((d,) + shape)
+        t[a] = 0.7
+        assert np.array_equal(assemble.apply_matrix_free(shape, E, C, t, element), np.zeros((d,) + shape))
+
+
+def test_matrix_free_operator_accuracy_on_smooth_fields():
+    """On a smooth field at 512^2 the matrix-free product keeps ~eps/theta relative
+    accuracy, against the same product evaluated in extended precision; the assembled
+    product, whose rounded entries no longer sum to zero per row, loses ~eps/theta^2."""
+    if np.finfo(np.longdouble).eps > 1e-18:
+        pytest.skip("no extended precision type on this platform")
+    shape = (512, 512)
+    E = material.young_from_density(smooth_density(shape, 16, 8.0, 0), 1e-2, 1.0, 2.0)
+    C = fe.C_unit(2, 0.3)
+    idx = np.indices(shape)
+    x = np.stack([np.cos(2 * np.pi * idx[0] / shape[0] + 0.3), 0.5 * np.sin(2 * np.pi * idx[1] / shape[1])])
+    ref = assemble.apply_matrix_free(shape, E.astype(np.longdouble), C.astype(np.longdouble), x.astype(np.longdouble))
+    scale = float(np.abs(ref).max())
+    mf = assemble.apply_matrix_free(shape, E, C, x)
+    asm = assemble.apply(assemble.assemble_K(shape, E, C), x)
+    assert float(np.abs(mf - ref).max()) <= 1e-13 * scale
+    assert float(np.abs(asm - ref).max()) > 1e-12 * scale

@@ -114,8 +114,10 @@ def test_dot_order_rounding_floor():
     the CG inner products agree to ~1e-15 in the first iterations; later the CG recurrence
     amplifies rounding until the gap is comparable to the iteration error itself. So iterate
     parity at 1e-10 is a property of early iterations or of tightly converged solves, not of
-    a run stopped at 1e-6: at tolerance tau both runs sit within ~tau of the exact solution
-    and their iteration counts agree within one."""
+    a run stopped at 1e-6: at tolerance tau both runs sit within ~tau of the exact solution.
+    Their counts are not fixed to one either: rounding delays Green-Jacobi convergence, so
+    the same iteration run in extended precision stops first and the FP64 runs stop up to
+    a few iterations later, the less accurate summation order last."""
     shape = (32, 32)
     E = material.young_from_density(smooth_density(shape, 16, 4.0, 0), 1e-4, 1.0, 2.0)
     prob = solve.setup(shape, E, 0.3)
@@ -126,10 +128,12 @@ def test_dot_order_rounding_floor():
         a = pcg.pcg(prob.apply_K, prob.minv("green_jacobi"), f, 0.0, k, dot_order="blas").x
         b = pcg.pcg(prob.apply_K, prob.minv("green_jacobi"), f, 0.0, k, dot_order="sequential").x
         assert np.linalg.norm(post.remove_mean(a) - post.remove_mean(b)) <= 1e-13 * nrm
+    ext = solve.setup(shape, E, 0.3, precision="extended")
     for tol in (1e-6, 1e-12):
         a = pcg.pcg(prob.apply_K, prob.minv("green_jacobi"), f, tol, 5000, dot_order="blas")
         b = pcg.pcg(prob.apply_K, prob.minv("green_jacobi"), f, tol, 5000, dot_order="sequential")
-        assert abs(a.iters - b.iters) <= 1
+        e = pcg.pcg(ext.apply_K, ext.minv("green_jacobi"), f.astype(ext.E.dtype), tol, 5000)
+        assert e.iters - 1 <= min(a.iters, b.iters) and max(a.iters, b.iters) <= e.iters + 3
         ua, ub = post.remove_mean(a.x), post.remove_mean(b.x)
         assert np.linalg.norm(ua - exact) <= 10 * tol * nrm
         assert np.linalg.norm(ua - ub) <= 10 * tol * nrm
