@@ -10,10 +10,10 @@ Workload (one "step" = one pass of the whole path over the sweep):
   Per contrast: material setup (E, J^1/2, Alg. 1 symbol) + one Green-Jacobi solve
   and one Green solve of the three loads -> 18 PCG solves per step.
 
-value: solves/s with the density field resident in HBM and outputs written to
-device buffers; e2e: the same through the C ABI with host buffers (pinned), the
-host->device copy of the density and the device->host read of u, C_hom, iteration
-counts and residuals inside the timed region.
+value: solves/s with the density field resident in HBM and every output of
+jfft_solve (u, element stress, C_hom, iteration counts, residuals) written to device
+buffers; e2e: the same through the C ABI with host buffers (pinned), the host->device
+copy of the density and the device->host read of every output inside the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank runs an independent replica (the path has no
@@ -49,6 +49,21 @@ WORKLOAD = ("2D plane-strain periodic cell, 1024x1024 Q1 quads (4 Gauss points),
             "(16 Fourier modes, |k|<=8), E = 1/c + (1-1/c) rho^2, c in {1e2,1e4,1e6}, nu 0.3, C_ref mean; "
             "3 Mandel unit loads; Green-Jacobi and Green PCG to 1e-8 relative residual")
 PROFILED_STEPS = 1   # steps of the per-kernel profiling pass after the timed steps
+SQRT2 = math.sqrt(2.0)
+# 3D configurations (trilinear hexes, 8 Gauss points, nu 0.3, E = 1/c + (1 - 1/c) rho^3,
+# Green-Jacobi PCG to a relative residual of 1e-8): one timed solve per precision.
+CONFIGS_3D = {
+    "3d_128": {"shape": (128, 128, 128), "modes": 32, "kmax": 6.0, "contrast": 1e5,
+               "loads": np.eye(6), "precisions": ("fp64", "mixed"),
+               "workload": ("3D periodic cell, 128^3 trilinear hexes (8 Gauss points), smooth density (32 Fourier "
+                            "modes, |k|<=6), E = 1/c + (1-1/c) rho^3, c = 1e5, nu 0.3; all 6 Mandel unit loads in "
+                            "one batched solve; Green-Jacobi PCG to 1e-8 relative residual")},
+    "3d_512": {"shape": (512, 512, 512), "modes": 32, "kmax": 12.0, "contrast": 1e6,
+               "loads": np.array([[0.0, 0.0, 0.0, 0.0, 0.0, SQRT2]]), "precisions": ("fp64", "mixed", "mixed_bf16"),
+               "workload": ("3D periodic cell, 512^3 trilinear hexes (8 Gauss points, 4.0e8 DOF), smooth density "
+                            "(32 Fourier modes, |k|<=12), E = 1/c + (1-1/c) rho^3, c = 1e6, nu 0.3; single load "
+                            "eps_xy = 1 (Mandel sqrt(2) e_6); Green-Jacobi PCG to 1e-8 relative residual")},
+}
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # SMs x max clock x FP64 flop/clk/SM (2 DFMA)
 ITER_COUNTS = os.path.join(ROOT, "oracle", "data", "iters_2d_1024.json")
 
@@ -127,56 +142,162 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def flops_per_unit(kernel, shape, d=2):
-    kernel = kernel[:-4] if kernel.endswith("_f32") else kernel
+def operator_flops_per_element(d):
+    """FP64/FP32 operations of the Walsh-Hadamard mode-form Q1 element (csrc/element.cuh),
+    counted by walking the same loops: the forward butterfly of d components (d stages of
+    2^(d-1) add/sub pairs), the mode-force map (one FMA per normal term and per shear
+    term, FMA = 2 flops), the E scaling (the force-free zero mode left out), the
+    transposed butterfly and the accumulation of the corner forces into the nodes.
+    70 in 2D, 309 in 3D."""
+    nc = 1 << d
+    popc = lambda m: bin(m).count("1")  # noqa: E731
+    mbit = lambda a: 1 << (d - 1 - a)  # noqa: E731
+    fma = 0
+    for mu in range(nc):
+        if popc(mu) >= d:
+            continue
+        for a in range(d):
+            if mu & mbit(a):
+                continue
+            fma += sum(1 for b in range(d) if not mu & mbit(b))
+            fma += sum(2 for b in range(d) if not mu & mbit(b) and b != a)
+            fma += sum(1 for c in range(d) if mu & mbit(c))
+    wht = d * d * (nc // 2) * 2
+    return wht + 2 * fma + d * (nc - 1) + wht + d * nc
+
+
+def _grid_terms(shape):
+    d = len(shape)
+    N = int(np.prod(shape))
+    F = N // shape[-1] * (shape[-1] // 2 + 1)
+    return d, N, F
+
+
+def flops_per_unit(kernel, shape):
     """Algorithmic FLOPs of one kernel for one load case (one right-hand side).
 
     FFT passes use the conventional 5 L log2 L per complex transform of length L
     (2.5 n log2 n for a real transform of length n); the symbol block multiply of a
     real symmetric d x d block by a complex vector costs 2 d^2 mults + 2 d (d-1)
-    adds per frequency; J^1/2 scalings one multiply per real value. The Q1 operator
-    counts the flops of its Walsh-Hadamard mode form (74 per node in 2D, see the
-    design notes), FMA = 2 flops."""
-    n0, n1 = shape
-    N = n0 * n1
-    M = n1 // 2
-    F = n0 * (M + 1)
-    if kernel == "fft_lines":
-        return d * (M + 1) * 2 * 5 * n0 * math.log2(n0) + F * (2 * d * d * 2 + 2 * d * (d - 1))
-    if kernel == "fft_rows_real_fwd":
-        return d * n0 * 2.5 * n1 * math.log2(n1) + d * N          # + J^1/2 scaling
-    if kernel == "fft_cols_real_inv":
-        return d * n0 * 2.5 * n1 * math.log2(n1) + 3 * d * N      # + J^1/2 scaling and r.z
-    if kernel == "apply_K":
-        return 74 * N + 2 * d * N                                  # operator + fused p.q
+    adds per frequency; J^1/2 scalings one multiply per real value; the operator the
+    mode-form count of operator_flops_per_element per node plus the fused p.q."""
+    k = kernel[:-4] if kernel.endswith("_f32") else kernel
+    d, N, F = _grid_terms(shape)
+    n = shape
+    rows = N // n[-1]                            # real lines along the last axis
+    real_fft = d * rows * 2.5 * n[-1] * math.log2(n[-1])
+    if k == "fft_rows_real_fwd":
+        return real_fft + d * N
+    if k == "fft_cols_real_inv":
+        return real_fft + 3 * d * N
+    if k in ("fft_rows_cplx_fwd", "fft_cols_cplx_inv"):   # 3D middle axis
+        return d * (F // n[1]) * 5 * n[1] * math.log2(n[1])
+    if k == "fft_lines":
+        return d * (F // n[0]) * 2 * 5 * n[0] * math.log2(n[0]) + F * (2 * d * d * 2 + 2 * d * (d - 1))
+    if k == "apply_K":
+        return operator_flops_per_element(d) * N + 2 * d * N
     return None
 
 
-def traffic_bytes_per_unit(kernel, shape, d=2):
+def traffic_bytes_per_unit(kernel, shape, material_bytes=None):
     """Compulsory DRAM bytes of one kernel for one load case; kernels whose name ends in
-    _f32 move FP32 data (s = 4 bytes per real), the others FP64 (s = 8)."""
+    _f32 move FP32 data (s = 4 bytes per real), the others FP64 (s = 8). The material
+    field is read once per launch for all loads; it is charged to each load here at
+    ``material_bytes`` per voxel (s by default, 2 for a BF16 copy)."""
     s = 4 if kernel.endswith("_f32") else 8
+    se = s if material_bytes is None else material_bytes
     k = kernel[:-4] if kernel.endswith("_f32") else kernel
-    n0, n1 = shape
-    N = n0 * n1
-    F = n0 * (n1 // 2 + 1)
+    d, N, F = _grid_terms(shape)
+    ncmp = d * (d + 1) // 2
     table = {
-        "fft_lines": 2 * d * F * 2 * s + F * 3 * s,              # spectrum in + out, symbol table
+        "fft_lines": 2 * d * F * 2 * s + F * ncmp * s,           # spectrum in + out, symbol table
         "fft_rows_real_fwd": d * N * s + d * F * 2 * s + N * s,   # r, spectrum, J^1/2 scale
+        "fft_rows_cplx_fwd": 2 * d * F * 2 * s,                   # spectrum in + out
+        "fft_cols_cplx_inv": 2 * d * F * 2 * s,
         "fft_cols_real_inv": d * F * 2 * s + 2 * d * N * s + N * s,   # spectrum, z, r (dot), scale
-        "apply_K": 2 * d * N * s + N * s,                         # p, q, E
+        "apply_K": 2 * d * N * s + N * se,                        # p, q, E
         "cg_xr": 6 * d * N * s,                                   # x, r read+write, p, q
         "cg_p": 3 * d * N * s,                                    # p read+write, z
     }
     return table.get(k)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch with all three
-# loads active, from the ncu capture summarised in profiles/fp64_2d_1024_gj_kernels.md
-# (1024 x 1024, Green-Jacobi, contrast 1e4), for kernels unchanged since that capture; the
-# FP32 kernels have no capture of all three loads active (their traffic stays null).
-NCU_TRAFFIC_PER_LAUNCH = {"fft_lines": 63.11e6 + 0.93e6, "apply_K": 59.86e6 + 11.20e6,
-                          "fft_cols_real_inv": 110.95e6 + 25.91e6, "fft_rows_real_fwd": 59.18e6 + 13.78e6}
+def source_fingerprint():
+    """sha256 (16 hex digits) over the CUDA sources, the header and the build flags: an
+    ncu capture is only reported next to the kernels it measured."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2508_02613_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    files += [os.path.join(ROOT, "include", "jfft.h"), os.path.join(ROOT, "paper_2508_02613_gb300", "build.py")]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) recorded in the
+    committed ncu summaries under profiles/, as lines
+        traffic: workload=<w> kernel=<k> loads=<n> dram_bytes=<b> sources=<fingerprint>
+    Only lines whose fingerprint matches the current sources are used: a capture of an
+    older kernel reads as no capture. Returns {kernel: (bytes per launch, loads, file)}."""
+    out = {}
+    fp = source_fingerprint()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return out
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, name)) as fh:
+            for line in fh:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line[len("traffic:"):].split() if "=" in t)
+                if kv.get("workload") == workload and kv.get("sources") == fp:
+                    out[kv["kernel"]] = (float(kv["dram_bytes"]), int(kv.get("loads", 1)), name)
+    return out
+
+
+def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_steps=1):
+    """Dominant kernel with its achieved rate, from the per-kernel CUDA events (summed event
+    time per kernel name) of a profiling pass that repeats the timed work. Units are
+    right-hand-side applications: per load, one operator and one preconditioner per PCG
+    iteration; ``n_units`` of them in the profiled pass. ``alu``: report against the FP64
+    ALU peak derived from the unit counts (FP64 kernels), else against measured HBM."""
+    rows = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda r: -r[2])
+    total_ms = sum(r[2] for r in rows)
+    peak_gbs, peak_kind = hbm_peak_gbs()
+    captured = ncu_traffic(workload)
+    for name, nl, tot in rows:
+        byt = traffic_bytes_per_unit(name, shape, material_bytes)
+        fl = flops_per_unit(name, shape)
+        if byt is None or fl is None:
+            continue
+        out = {"kernel": name, "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
+               "units": n_units, "algorithmic_bytes_per_unit": byt, "algorithmic_flops_per_unit": fl,
+               "traffic": None}
+        if name in captured:
+            tb, loads, src = captured[name]
+            out["traffic"] = tb
+            out["traffic_note"] = (f"ncu DRAM bytes of one launch with {loads} load(s) active ({src}); the "
+                                   f"algorithmic bytes of that launch are {loads * byt:.4g}")
+        else:
+            out["traffic_note"] = "no ncu capture of the current kernel sources for this workload"
+        gbs = n_units * byt / (tot / 1e3) / 1e9
+        tfl = n_units * fl / (tot / 1e3) / 1e12
+        if alu:
+            out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": tfl / FP64_PEAK_TFLOPS, "hbm_GBps_algorithmic": gbs,
+                        "peak_note": "FP64 ALU, derived: 152 SMs x 2.07 GHz x 4 flop/clk/SM (2 DFMA)"})
+        else:
+            out.update({"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
+                        "peak_note": f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"})
+        return out
+    return None
 
 
 def aggregate(ms_local, world, solves_per_step, dist=None, device=None):
@@ -243,6 +364,90 @@ def oracle_iteration_counts():
             continue
         out.setdefault((r["contrast"], r["precond"]), [0, 0, 0])[r["load"]] = r["iters"]
     return out
+
+
+# Small instances of the benchmark recipes on which every mixed-precision result is
+# compared with the oracle solved to 1e-13 (the full-size grids are beyond the oracle's
+# reach inside a benchmark run): the 2D sweep's recipe at 32^2 and 256^2 (contrast 1e4,
+# rho^2, 3 loads) and the 3D recipe at 16^3 (32 modes |k| <= 6, rho^3, contrast 1e5, 6 loads).
+ERR_CASES = {
+    "2d_32": {"shape": (32, 32), "modes": 16, "kmax": 8.0, "exponent": 2.0, "contrast": 1e4, "nloads": 3},
+    "2d_256": {"shape": (256, 256), "modes": 16, "kmax": 8.0, "exponent": 2.0, "contrast": 1e4, "nloads": 3},
+    "3d_16": {"shape": (16, 16, 16), "modes": 32, "kmax": 6.0, "exponent": 3.0, "contrast": 1e5, "nloads": 6},
+}
+
+
+def oracle_reference_solutions(path):
+    """Oracle solutions (Green-Jacobi PCG to 1e-13, zero-mean u and C_hom) of ERR_CASES,
+    written to ``path`` (npz); part of the CPU-side leg, run before any CUDA call."""
+    from oracle import material, solve as osolve
+    from synthetic import smooth_density
+    arrays = {}
+    for key, c in ERR_CASES.items():
+        rho = smooth_density(c["shape"], c["modes"], c["kmax"], SEED)
+        E = material.young_from_density(rho, 1.0 / c["contrast"], 1.0, c["exponent"])
+        prob = osolve.setup(c["shape"], E, NU)
+        ref = osolve.solve(prob, np.eye(c["nloads"]), 1e-13, "green_jacobi")
+        arrays[key + "_u"] = ref.u
+        arrays[key + "_C_hom"] = ref.C_hom
+    np.savez(path, **arrays)
+
+
+def run_oracle_reference_subprocess(path):
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"import bench; bench.oracle_reference_solutions({path!r})"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                       stderr=subprocess.PIPE, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle reference solutions failed: " + r.stderr[-2000:])
+    return dict(np.load(path))
+
+
+def cpu_openmp_sample():
+    """The C PCG baseline (oracle/cbase: matrix-free operator, textbook radix-2 FFT, OpenMP
+    on every host core) on a bounded sample: at 1024 x 1024 (contrast 1e4) the oracle's
+    setup (not part of the C code), one full Green-Jacobi solve of load 0 to 1e-8 and five
+    Green iterations; the 32 x 32 configuration (16 modes |k| <= 4, contrast 1e4, rho^2,
+    eps_xx, tolerance 1e-6) solved in full with both preconditioners."""
+    from oracle import assemble, cbase, material, solve as osolve
+    from synthetic import smooth_density
+    out = {"threads": cbase.threads()}
+    rho = smooth_density(SHAPE, MODES, KMAX, SEED)
+    E = material.young_from_density(rho, 1e-4, 1.0, EXPONENT)
+    t0 = time.perf_counter()
+    prob = osolve.setup(SHAPE, E, NU)
+    out["t_setup"] = time.perf_counter() - t0
+    f = assemble.assemble_rhs(SHAPE, E, prob.C, np.eye(3)[0])
+    t0 = time.perf_counter()
+    _, it, conv = cbase.pcg(prob, f, TOL, "green_jacobi")
+    out["gj_full_solve_s"], out["gj_full_iters"], out["gj_converged"] = time.perf_counter() - t0, it, conv
+    t0 = time.perf_counter()
+    cbase.pcg(prob, f, 0.0, "green", max_iter=5)
+    out["t_iter"] = {"green_jacobi": out["gj_full_solve_s"] / max(it, 1), "green": (time.perf_counter() - t0) / 5}
+    small = (32, 32)
+    rho32 = smooth_density(small, 16, 4.0, 0)
+    E32 = material.young_from_density(rho32, 1e-4, 1.0, 2.0)
+    p32 = osolve.setup(small, E32, NU)
+    f32 = assemble.assemble_rhs(small, E32, p32.C, np.eye(3)[0])
+    out["c1_32"] = {}
+    for pc in PRECONDS:
+        reps, t0 = 0, time.perf_counter()
+        while reps < 3 or time.perf_counter() - t0 < 0.5:
+            _, it32, _ = cbase.pcg(p32, f32, 1e-6, pc)
+            reps += 1
+        out["c1_32"][pc] = {"iters": it32, "s_per_solve": (time.perf_counter() - t0) / reps}
+    return out
+
+
+def run_cpu_openmp_subprocess():
+    env = dict(os.environ, OMP_NUM_THREADS=str(os.cpu_count() or 1), OPENBLAS_NUM_THREADS="1")
+    code = "import json, bench; print('CPUOMP ' + json.dumps(bench.cpu_openmp_sample()))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, stdout=subprocess.PIPE,
+                       stderr=subprocess.PIPE, text=True, timeout=900)
+    for line in r.stdout.splitlines():
+        if line.startswith("CPUOMP "):
+            return json.loads(line[len("CPUOMP "):])
+    raise RuntimeError("C baseline sample failed: " + r.stderr[-2000:])
 
 
 def run_cpu_sample_subprocess():
@@ -317,6 +522,9 @@ def main():
     ap.add_argument("--no-cells", action="store_true", help="skip the small-cell batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-material variant of the mixed leg")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D legs (128^3 x 6 loads, 512^3)")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT timing cross-check")
+    ap.add_argument("--only-3d", default="", help="run only these 3D legs (comma list of CONFIGS_3D keys)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel from the host (profilers cannot see kernels inside conditional graphs)")
     ap.add_argument("--serving-requests", type=int, default=40,
@@ -331,8 +539,14 @@ def main():
 
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     cpu = None
+    cpu_omp = None
+    oracle_ref = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_sample_subprocess()   # before any CUDA call in this process
+        cpu_omp = run_cpu_openmp_subprocess()
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            oracle_ref = run_oracle_reference_subprocess(os.path.join(td, "oracle_ref.npz"))
 
     import torch
     torch.cuda.set_device(local)
@@ -377,7 +591,7 @@ def main():
                     if record is not None:
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
-                    out = s.solve(eps_d, TOL, pc, want_stress=False)
+                    out = s.solve(eps_d, TOL, pc, want_stress=True)
                     if record is not None:
                         e1.record(stream)
                         e1.synchronize()
@@ -432,40 +646,10 @@ def main():
         s.set_profiling(False)
         s.close()
         ms, value = aggregate(statistics.mean(times), world, solves_per_step, dist, "cuda")
-        return {"ms": ms, "value": value, "times": times, "rec": rec, "prof": prof, "launches": launches,
+        return {"precision": precision, "ms": ms, "value": value, "times": times, "rec": rec, "prof": prof,
+                "launches": launches,
                 "graph_replays": replays, "profiled_step_ms": prof_times, "tuning": tuning,
                 "clocks": clk}
-
-    def roofline(leg, alu):
-        """Dominant kernel with its achieved rate, from the per-kernel CUDA events of the
-        profiling pass that repeats the timed steps. Units are right-hand-side applications:
-        per load, one operator and one preconditioner per PCG iteration."""
-        n_units = sum(sum(r["iters"]) for r in leg["rec"].values()) * PROFILED_STEPS
-        rows = sorted(((k, v[0], v[1]) for k, v in leg["prof"].items()), key=lambda r: -r[2])
-        total_ms = sum(r[2] for r in rows)
-        peak_gbs, peak_kind = hbm_peak_gbs()
-        for name, nl, tot in rows:
-            byt = traffic_bytes_per_unit(name, SHAPE)
-            fl = flops_per_unit(name, SHAPE)
-            if byt is None or fl is None:
-                continue
-            out = {"kernel": name, "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
-                   "traffic": None, "algorithmic_bytes_per_unit": byt, "units": n_units}
-            if name in NCU_TRAFFIC_PER_LAUNCH:
-                out["traffic"] = NCU_TRAFFIC_PER_LAUNCH[name]
-                out["traffic_note"] = ("DRAM bytes of one 3-load launch (ncu); the algorithmic bytes of that "
-                                       f"launch are {3 * byt:.4g} (L2 keeps part of the fields)")
-            gbs = n_units * byt / (tot / 1e3) / 1e9
-            tfl = n_units * fl / (tot / 1e3) / 1e12
-            if alu:
-                out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": tfl / FP64_PEAK_TFLOPS, "hbm_GBps_algorithmic": gbs,
-                            "peak_note": "FP64 ALU: 152 SMs x 2.07 GHz x 4 flop/clk/SM (probe: 1.197 TFLOP/s DFMA)"})
-            else:
-                out.update({"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
-                            "peak_note": f"HBM copy bandwidth, {peak_kind} (burst)"})
-            return out
-        return None
 
     def cells_leg():
         """The 32 x 32 workload (16 modes |k| <= 4, seeds 0-9, E = 1e-4 + (1 - 1e-4) rho^2,
@@ -583,6 +767,136 @@ def main():
                 "served_mixed_first8_run_s_sum": served_first,
                 "note": "offered load exceeds capacity, so latency percentiles are queue-dominated"}
 
+    def leg_3d(key):
+        """One configuration of CONFIGS_3D: per precision a solver on the device-resident
+        density, one warm-up solve, one timed solve (CUDA events on the solver's stream, L2
+        flushed before), one profiled solve (per-kernel CUDA events) for the roofline."""
+        from synthetic import smooth_density_device
+        cfg = CONFIGS_3D[key]
+        shape = cfg["shape"]
+        rho3 = smooth_density_device(shape, cfg["modes"], cfg["kmax"], SEED)
+        rho3_h = rho3.cpu().numpy()
+        loads = torch.tensor(cfg["loads"], device="cuda")
+        out = {"workload": cfg["workload"], "grid": list(shape), "loads": int(cfg["loads"].shape[0]), "tol": TOL,
+               "dof_per_load": 3 * int(np.prod(shape))}
+        for prec in cfg["precisions"]:
+            bf = prec == "mixed_bf16"
+            s3 = Solver(shape, rho3_h, NU, kind="density", e_min=1.0 / cfg["contrast"], e_max=1.0, exponent=3.0,
+                        stream=stream.cuda_stream, io="device", max_loads=max(3, len(cfg["loads"])),
+                        precision="fp64" if prec == "fp64" else "mixed", material_bf16=bf,
+                        graphs=not args.no_graphs, autotune=True)
+            s3.solve(loads, TOL, "green_jacobi", want_stress=True)   # warm-up
+            flush.fill_(1.0)
+            barrier()
+            n0 = s3.launch_count
+            clocks = ClockSampler(smi_id)
+            clocks.start()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = s3.solve(loads, TOL, "green_jacobi", want_stress=True)
+            e1.record(stream)
+            barrier()
+            clk = clocks.stop()
+            ms = e0.elapsed_time(e1)
+            launches = s3.launch_count - n0
+            iters = [int(v) for v in res["iters"].cpu().tolist()]
+            rec = {"time_to_tol_ms": ms, "solves_per_s": len(iters) / (ms / 1e3), "iters": iters,
+                   "refine_steps": [int(v) for v in res["refine_steps"].cpu().tolist()],
+                   "rel_res": [float(v) for v in res["rel_res"].cpu().tolist()],
+                   "converged": int(res["status"]) == 0, "gpu_launches": launches, "clocks": clk,
+                   "workspace_gb": s3.workspace_bytes / 1e9, "tuning": s3.tuning,
+                   "dtype": "f64" if prec == "fp64" else ("f32 inner PCG, bf16 material copy, f64 scalars, residual "
+                                                          "and solution" if bf else
+                                                          "f32 inner PCG, f64 scalars, residual and solution")}
+            s3.set_profiling(True)
+            flush.fill_(1.0)
+            barrier()
+            s3.solve(loads, TOL, "green_jacobi", want_stress=True)
+            barrier()
+            prof = s3.profile()
+            s3.set_profiling(False)
+            rec["kernels_ms_total"] = {k: round(v[1], 3) for k, v in prof.items()}
+            rec["roofline"] = roofline(prof, sum(iters), shape, prec == "fp64", f"{key}_{prec}",
+                                       material_bytes=2 if bf else None)
+            s3.close()
+            del res
+            torch.cuda.empty_cache()
+            out[prec] = rec
+        if "fp64" in out:
+            for prec in cfg["precisions"]:
+                if prec != "fp64":
+                    out[prec]["speedup_vs_fp64"] = out["fp64"]["time_to_tol_ms"] / out[prec]["time_to_tol_ms"]
+        del rho3, loads
+        torch.cuda.empty_cache()
+        return out
+
+    def err_vs_oracle(precision, material_bf16, keys):
+        """Relative L2 error of u and max relative error of C_hom of this precision's GPU solve
+        (Green-Jacobi to 1e-8, every load of the case) against the oracle's 1e-13 solution,
+        per ERR_CASES instance; worst load reported."""
+        if oracle_ref is None:
+            return None
+        out = {}
+        for key in keys:
+            c = ERR_CASES[key]
+            rho_c = smooth_density(c["shape"], c["modes"], c["kmax"], SEED)
+            sc = Solver(c["shape"], rho_c, NU, kind="density", e_min=1.0 / c["contrast"], e_max=1.0,
+                        exponent=c["exponent"], max_loads=max(c["nloads"], 3), precision=precision,
+                        material_bf16=material_bf16, stream=stream.cuda_stream)
+            res = sc.solve(np.eye(c["nloads"]), TOL, "green_jacobi")
+            sc.close()
+            u_ref, ch_ref = oracle_ref[key + "_u"], oracle_ref[key + "_C_hom"]
+            du = max(float(np.linalg.norm(res["u"][g] - u_ref[g]) / np.linalg.norm(u_ref[g]))
+                     for g in range(c["nloads"]))
+            dc = float(np.abs(res["C_hom"] - ch_ref).max() / np.abs(ch_ref).max())
+            out[key] = {"u_rel_l2": du, "C_hom_rel": dc, "rel_res_max": float(res["rel_res"].max()),
+                        "tol": TOL, "grid": list(c["shape"]), "contrast": c["contrast"], "loads": c["nloads"]}
+        return out
+
+    def cufft_leg():
+        """Timing cross-check only; cuFFT (through torch.fft) is on no path of the solver. The
+        forward real 2D transform and its inverse of the fields one 1024^2 preconditioner
+        application transforms (3 loads x 2 components), beside the transform passes of this
+        library's Green-Jacobi preconditioner on the same number of fields (its per-kernel CUDA
+        events during jfft_apply_precond: J^1/2 scaling, forward transform, symbol block
+        multiply, inverse transform, J^1/2 scaling and r.z), FP64 and FP32; L2 flushed before
+        every repetition."""
+        out = {"fields": f"{N_LOADS} loads x 2 components, {SHAPE[0]}x{SHAPE[1]}", "reps": 10}
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(7)
+        for prec, dt in (("fp64", torch.float64), ("mixed", torch.float32)):
+            x = torch.randn((N_LOADS, 2) + SHAPE, dtype=dt, device="cuda", generator=gen)
+            pair = lambda: torch.fft.irfftn(torch.fft.rfftn(x, dim=(-2, -1)), s=SHAPE, dim=(-2, -1))  # noqa: E731
+            for _ in range(3):
+                pair()
+            ts = []
+            for _ in range(out["reps"]):
+                flush.fill_(1.0)
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pair()
+                e1.record(stream)
+                barrier()
+                ts.append(e0.elapsed_time(e1))
+            sp = Solver(SHAPE, rho_h, NU, kind="density", e_min=1e-4, e_max=1.0, exponent=EXPONENT,
+                        stream=stream.cuda_stream, io="device", max_loads=N_LOADS, precision=prec)
+            r = torch.randn((N_LOADS, 2) + SHAPE, dtype=torch.float64, device="cuda", generator=gen)
+            for _ in range(3):
+                sp.apply_precond("green_jacobi", r)
+            sp.set_profiling(True)
+            for _ in range(out["reps"]):
+                flush.fill_(1.0)
+                barrier()
+                sp.apply_precond("green_jacobi", r)
+            prof = sp.profile()
+            sp.set_profiling(False)
+            sp.close()
+            passes = {k: v[1] / out["reps"] for k, v in prof.items() if k.startswith("fft_")}
+            out[prec] = {"cufft_r2c_c2r_ms": statistics.median(ts), "preconditioner_passes_ms": sum(passes.values()),
+                         "passes_ms": {k: round(v, 4) for k, v in passes.items()}}
+        return out
+
     legs = args.legs.split(",")
     fp64 = run_leg("fp64") if "fp64" in legs else None
     mixed = run_leg("mixed") if "mixed" in legs else None
@@ -592,7 +906,8 @@ def main():
     ms, value, launches = fp64["ms"], fp64["value"], fp64["launches"]
     iters = {k: v["iters"] for k, v in fp64["rec"].items()}
     prof = fp64["prof"]
-    roof = roofline(fp64, alu=True)
+    n_units_fp64 = sum(sum(r["iters"]) for r in fp64["rec"].values()) * PROFILED_STEPS
+    roof = roofline(prof, n_units_fp64, SHAPE, fp64["precision"] == "fp64", "2d_1024_sweep")
 
     # ---- e2e through the C ABI with host buffers (FP64, the value's configuration)
     e2e = None
@@ -609,9 +924,10 @@ def main():
                 sh.set_material(rho_pin, e_min=1.0 / c)
                 h2d += rho_pin.nbytes
                 for pc in PRECONDS:
-                    out = sh.solve(eps_h, TOL, pc, want_stress=False)
+                    out = sh.solve(eps_h, TOL, pc, want_stress=True)
                     h2d += eps_h.nbytes
-                    d2h += out["u"].nbytes + out["C_hom"].nbytes + out["iters"].nbytes + out["rel_res"].nbytes
+                    d2h += (out["u"].nbytes + out["stress"].nbytes + out["C_hom"].nbytes + out["iters"].nbytes
+                            + out["rel_res"].nbytes + out["refine_steps"].nbytes)
 
         for _ in range(3):
             step_host()
@@ -627,13 +943,23 @@ def main():
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
         sh.close()
 
+    legs_3d = {}
+    if not args.no_3d:
+        for key in (args.only_3d.split(",") if args.only_3d else CONFIGS_3D):
+            legs_3d[key] = leg_3d(key)
+            for prec in legs_3d[key]:
+                if prec in ("mixed", "mixed_bf16"):
+                    legs_3d[key][prec]["err_vs_oracle"] = err_vs_oracle("mixed", prec == "mixed_bf16", ("3d_16",))
+    cufft_line = cufft_leg() if not args.no_cufft else None
     cells_line = cells_leg() if not args.no_cells else None
     serving_line = serving_leg() if not args.no_serving else None
 
     mixed_line = None if mixed is None else {
         "value": mixed["value"], "unit": "solves/s", "ms_per_step": mixed["ms"], "speedup_vs_fp64": fp64["ms"] / mixed["ms"],
         "dtype": "f32 inner PCG (operator, FFT, preconditioner, vectors) + f64 scalars, residual and solution",
-        "roofline": roofline(mixed, alu=False), "clocks": mixed["clocks"], "gpu_launches": mixed["launches"] // args.steps,
+        "roofline": roofline(mixed["prof"], sum(sum(r["iters"]) for r in mixed["rec"].values()) * PROFILED_STEPS,
+                             SHAPE, False, "2d_1024_sweep_mixed"),
+        "clocks": mixed["clocks"], "gpu_launches": mixed["launches"] // args.steps,
         "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in mixed["rec"].items()},
         "iters": {f"{pc}@{c:g}": v["iters"] for (c, pc), v in mixed["rec"].items()},
         "refine_steps": {f"{pc}@{c:g}": v["refine"] for (c, pc), v in mixed["rec"].items()},
@@ -643,6 +969,8 @@ def main():
         "tuning": mixed["tuning"],
         "profiled_step_ms": mixed["profiled_step_ms"],
     }
+    if mixed_line is not None:
+        mixed_line["err_vs_oracle"] = err_vs_oracle("mixed", False, ("2d_32", "2d_256"))
     if mixed_line is not None and bf16 is not None:
         mixed_line["material_bf16"] = {
             "value": bf16["value"], "unit": "solves/s", "ms_per_step": bf16["ms"],
@@ -650,7 +978,8 @@ def main():
             "note": "mixed precision with the FP32 operator reading E from a BF16 copy (options.material_bf16)",
             "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in bf16["rec"].items()},
             "iters": {f"{pc}@{c:g}": v["iters"] for (c, pc), v in bf16["rec"].items()},
-            "rel_res_max": max(max(v["rel_res"]) for v in bf16["rec"].values())}
+            "rel_res_max": max(max(v["rel_res"]) for v in bf16["rec"].values()),
+            "err_vs_oracle": err_vs_oracle("mixed", True, ("2d_32", "2d_256"))}
     clk = fp64["clocks"]
     times = fp64["times"]
 
@@ -663,6 +992,20 @@ def main():
                                "GPU run's iteration counts"),
                     "cpu": cpu_model(), "sample_seconds": cpu}
 
+    cpu_omp_line = None
+    if cpu_omp is not None:
+        step_s = len(CONTRASTS) * cpu_omp["t_setup"] + sum(
+            n * cpu_omp["t_iter"][pc] for (c, pc), its in iters.items() for n in its)
+        cpu_omp_line = {
+            "value": solves_per_step / step_s, "unit": "solves/s", "cores": cpu_omp["threads"], "kind": "c_openmp",
+            "sample": ("oracle/cbase (matrix-free Q1 operator, textbook radix-2 FFT, OpenMP, FP64): one full "
+                       "Green-Jacobi solve at 1024x1024 (contrast 1e4, load 0, tol 1e-8) and 5 Green iterations, "
+                       "the Python oracle's setup per contrast; scaled to this step's 18 solves with the GPU "
+                       "run's iteration counts"),
+            "gj_full_solve_1024_s": cpu_omp["gj_full_solve_s"], "gj_full_solve_1024_iters": cpu_omp["gj_full_iters"],
+            "s_per_iter_1024": cpu_omp["t_iter"], "setup_s_1024": cpu_omp["t_setup"],
+            "small_32x32_full_solves": cpu_omp["c1_32"], "cpu": cpu_model()}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -673,8 +1016,11 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written before each timed step (outside the timed interval)",
                        "launch_shapes": "plan-time autotuner (options.autotune)"},
-            "roofline": roof, "cpu_baseline": cpu_line, "e2e": e2e, "gpu_launches": launches // args.steps,
-            "clocks": clk, "mixed": mixed_line, "small_cells": cells_line, "serving": serving_line,
+            "roofline": roof, "cpu_baseline": cpu_line, "cpu_openmp_baseline": cpu_omp_line, "e2e": e2e,
+            "gpu_launches": launches // args.steps,
+            "clocks": clk, "mixed": mixed_line, "configs_3d": legs_3d, "cufft_crosscheck": cufft_line,
+            "small_cells": cells_line,
+            "serving": serving_line,
             "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
                        "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in fp64["rec"].items()},
                        "rel_res_max": max(max(v["rel_res"]) for v in fp64["rec"].values()),

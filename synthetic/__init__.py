@@ -8,6 +8,7 @@ oracle and the CUDA path can both consume its output without sharing method code
 
 from .fields import (  # noqa: F401
     smooth_density,
+    smooth_density_device,
     laminate_density,
     cosine_density,
     random_field,

@@ -33,6 +33,44 @@ def _nodal_coords(shape):
     return [np.arange(n, dtype=np.float64) / n for n in shape]
 
 
+def _smooth_modes(d: int, n_modes: int, k_max: float, seed: int):
+    """Steps 1-2 of the smooth_density recipe: wave vectors, amplitudes, phases."""
+    kmax_i = int(math.floor(k_max))
+    cands = [k for k in itertools.product(range(-kmax_i, kmax_i + 1), repeat=d)
+             if 0 < sum(c * c for c in k) <= k_max * k_max]
+    cands = np.array(cands, dtype=np.int64)
+    if n_modes > len(cands):
+        raise ValueError("n_modes exceeds the number of wave vectors with |k| <= k_max")
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(cands), size=n_modes, replace=False)
+    kvec = cands[pick]
+    amp = rng.standard_normal(n_modes)
+    phase = rng.uniform(0.0, 2.0 * math.pi, n_modes)
+    return kvec, amp, phase
+
+
+def smooth_density_device(shape, n_modes: int, k_max: float, seed: int, device="cuda"):
+    """The smooth_density recipe (same wave vectors, amplitudes and phases) evaluated as a
+    float64 torch tensor on ``device``: for grids whose host evaluation would take minutes
+    (512^3). Equal to smooth_density up to the rounding of the sum."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    d = len(shape)
+    kvec, amp, phase = _smooth_modes(d, n_modes, k_max, seed)
+    coords = _nodal_coords(shape)
+    fac = [torch.tensor(np.exp(2j * math.pi * np.outer(kvec[:, a], coords[a])), device=device) for a in range(d)]
+    coef = torch.tensor(amp * np.exp(1j * phase), device=device)
+    raw = torch.zeros(shape, dtype=torch.float64, device=device)
+    for m in range(n_modes):
+        t = coef[m] * fac[0][m]
+        for a in range(1, d):
+            t = t.reshape(t.shape + (1,)) * fac[a][m].reshape((1,) * a + (-1,))
+        raw += t.real
+        del t
+    lo, hi = raw.min(), raw.max()
+    return (raw - lo) / (hi - lo)
+
+
 def smooth_density(shape, n_modes: int, k_max: float, seed: int) -> np.ndarray:
     """Smooth random density rho in [0, 1] from a sum of Fourier modes.
 
@@ -48,17 +86,7 @@ def smooth_density(shape, n_modes: int, k_max: float, seed: int) -> np.ndarray:
     """
     shape = tuple(int(s) for s in shape)
     d = len(shape)
-    kmax_i = int(math.floor(k_max))
-    cands = [k for k in itertools.product(range(-kmax_i, kmax_i + 1), repeat=d)
-             if 0 < sum(c * c for c in k) <= k_max * k_max]
-    cands = np.array(cands, dtype=np.int64)
-    if n_modes > len(cands):
-        raise ValueError("n_modes exceeds the number of wave vectors with |k| <= k_max")
-    rng = np.random.default_rng(seed)
-    pick = rng.choice(len(cands), size=n_modes, replace=False)
-    kvec = cands[pick]
-    amp = rng.standard_normal(n_modes)
-    phase = rng.uniform(0.0, 2.0 * math.pi, n_modes)
+    kvec, amp, phase = _smooth_modes(d, n_modes, k_max, seed)
 
     # Separable evaluation, one slab of the first axis at a time, so that large
     # 3D grids do not need an n_modes x N temporary.
