@@ -518,16 +518,18 @@ def main():
     ap.add_argument("--contrasts", default=",".join(f"{c:g}" for c in CONTRASTS),
                     help="subset of the contrast sweep (profiling runs)")
     ap.add_argument("--preconds", default=",".join(PRECONDS), help="subset of the preconditioners (profiling runs)")
-    ap.add_argument("--legs", default="fp64,mixed", help="precision legs to run (profiling runs)")
+    ap.add_argument("--legs", default="fp64,mixed",
+                    help="precision legs of the 2D sweep (profiling runs); 'none' runs only the 3D legs")
     ap.add_argument("--no-cells", action="store_true", help="skip the small-cell batch leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-material variant of the mixed leg")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D legs (128^3 x 6 loads, 512^3)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT timing cross-check")
     ap.add_argument("--only-3d", default="", help="run only these 3D legs (comma list of CONFIGS_3D keys)")
+    ap.add_argument("--precisions-3d", default="", help="run only these precisions in the 3D legs (profiling runs)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch every kernel from the host (profilers cannot see kernels inside conditional graphs)")
-    ap.add_argument("--serving-requests", type=int, default=40,
+    ap.add_argument("--serving-requests", type=int, default=500,
                     help="requests of the seeded serving stream to replay (the full stream has 2000)")
     args = ap.parse_args()
     CONTRASTS = tuple(float(c) for c in args.contrasts.split(","))
@@ -740,8 +742,12 @@ def main():
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
-        lat = sorted(o["latency_s"] for o in outs)
-        pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+        def pct(vals, q):
+            v = sorted(vals)
+            return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+        lat = [o["latency_s"] for o in outs]
+        run = [o["run_s"] for o in outs]
+        que = [o["queued_s"] for o in outs]
         # serial plain FP64 on the first 8 requests
         t_ser = 0.0
         n_ser = min(8, n)
@@ -758,8 +764,12 @@ def main():
                              "log-U[1e2,1e6], nu U[0.2,0.4], 1..d* loads, Green-Jacobi to 1e-8, mixed precision"),
                 "requests": n, "of_stream": 2000, "offered_per_s": 50.0, "max_active": 4,
                 "wall_s": wall, "solves_per_s": n / wall,
-                "p50_latency_s": pct(0.50), "p99_latency_s": pct(0.99),
-                "mean_queue_s": statistics.mean(o["queued_s"] for o in outs),
+                "p50_latency_s": pct(lat, 0.50), "p99_latency_s": pct(lat, 0.99),
+                "p50_run_s": pct(run, 0.50), "p99_run_s": pct(run, 0.99),
+                "p50_queue_s": pct(que, 0.50), "p99_queue_s": pct(que, 0.99),
+                "mean_queue_s": statistics.mean(que),
+                "latency_note": ("latency = submission to result; run = start of the solve to result (without "
+                                 "queueing); queue = submission to start"),
                 "max_rel_res": max(float(o["rel_res"].max()) for o in outs),
                 "all_converged": all(o["status"] == 0 for o in outs),
                 "solvers": {k: st[k] for k in ("solvers_created", "solvers_reused", "solvers_evicted", "peak_used")},
@@ -779,7 +789,8 @@ def main():
         loads = torch.tensor(cfg["loads"], device="cuda")
         out = {"workload": cfg["workload"], "grid": list(shape), "loads": int(cfg["loads"].shape[0]), "tol": TOL,
                "dof_per_load": 3 * int(np.prod(shape))}
-        for prec in cfg["precisions"]:
+        precs = [p for p in cfg["precisions"] if not args.precisions_3d or p in args.precisions_3d.split(",")]
+        for prec in precs:
             bf = prec == "mixed_bf16"
             s3 = Solver(shape, rho3_h, NU, kind="density", e_min=1.0 / cfg["contrast"], e_max=1.0, exponent=3.0,
                         stream=stream.cuda_stream, io="device", max_loads=max(3, len(cfg["loads"])),
@@ -823,7 +834,7 @@ def main():
             torch.cuda.empty_cache()
             out[prec] = rec
         if "fp64" in out:
-            for prec in cfg["precisions"]:
+            for prec in precs:
                 if prec != "fp64":
                     out[prec]["speedup_vs_fp64"] = out["fp64"]["time_to_tol_ms"] / out[prec]["time_to_tol_ms"]
         del rho3, loads
@@ -898,6 +909,12 @@ def main():
         return out
 
     legs = args.legs.split(",")
+    if "none" in legs:
+        # profiling runs of the 3D legs alone: no 2D sweep, one JSON line with those legs
+        out3 = {key: leg_3d(key) for key in (args.only_3d.split(",") if args.only_3d else CONFIGS_3D)}
+        if rank == 0:
+            print(json.dumps({"configs_3d": out3, "note": "3D legs only (--legs none); no headline value"}))
+        return 0
     fp64 = run_leg("fp64") if "fp64" in legs else None
     mixed = run_leg("mixed") if "mixed" in legs else None
     bf16 = run_leg("mixed", material_bf16=True, light=True) if ("mixed" in legs and not args.no_bf16) else None
@@ -991,6 +1008,10 @@ def main():
                                "3 Green-Jacobi and 3 Green iterations, scaled to this step's 18 solves with the "
                                "GPU run's iteration counts"),
                     "cpu": cpu_model(), "sample_seconds": cpu}
+
+    if serving_line is not None and oracle_ref is not None:
+        # the served requests run the mixed-precision solver: its error on the 2D and 3D recipes
+        serving_line["err_vs_oracle"] = err_vs_oracle("mixed", False, ("2d_32", "2d_256", "3d_16"))
 
     cpu_omp_line = None
     if cpu_omp is not None:

@@ -105,3 +105,37 @@ def test_poisson_ratio_change_on_a_live_solver():
     oa = a.solve(mandel_unit_loads(2), 1e-8, "green_jacobi")
     ob = b.solve(mandel_unit_loads(2), 1e-8, "green_jacobi")
     assert np.array_equal(oa["u"], ob["u"]) and np.array_equal(oa["iters"], ob["iters"])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_served_results_match_the_oracle(precision):
+    """Small requests (32^2, 32 x 64, 8^3, 8 x 8 x 16; different contrasts, Poisson ratios, load sets
+    and preconditioners) served concurrently, against the FP64 oracle solved to 1e-13: the
+    served u is within the rigorous residual bound ||f - K u|| / lambda_min of the oracle's
+    (plus the oracle's own residual bound), C_hom within 10 tol."""
+    from oracle import assemble, material, solve as osolve
+    from paper_2508_02613_gb300.jfft import Server
+    from tests.test_gpu_mixed import error_bound
+    cases = [((32, 32), 1e3, 0.25, [0, 2], "green_jacobi"), ((32, 64), 1e5, 0.35, [1], "green"),
+             ((8, 8, 8), 1e3, 0.3, [0, 3, 5], "green_jacobi"), ((8, 8, 16), 1e4, 0.22, [5], "green_jacobi"),
+             ((32, 32), 1e2, 0.4, [0, 1, 2], "green")]
+    srv = Server(max_active=4)
+    subs = []
+    for i, (shape, contrast, nu, loads, pc) in enumerate(cases):
+        d = len(shape)
+        rho = smooth_density(shape, 12 if d == 2 else 16, 4.0, 300 + i)
+        eps = mandel_unit_loads(d)[loads]
+        rid = srv.submit(shape, rho, nu, eps, 1e-8, pc, precision, kind="density", e_min=1.0 / contrast, e_max=1.0,
+                         exponent=2.0, want_u=True)
+        subs.append((rid, shape, rho, contrast, nu, eps, pc))
+    for rid, shape, rho, contrast, nu, eps, pc in subs:
+        o = srv.wait(rid)
+        assert o["status"] == 0 and o["rel_res"].max() <= 1e-8 * 1.01
+        E = material.young_from_density(rho, 1.0 / contrast, 1.0, 2.0)
+        prob = osolve.setup(shape, E, nu)
+        ref = osolve.solve(prob, eps, 1e-13, pc)
+        assert np.abs(o["C_hom"] - ref.C_hom).max() <= 10 * 1e-8 * np.abs(ref.C_hom).max()
+        for g in range(len(eps)):
+            f = assemble.assemble_rhs(shape, E, prob.C, eps[g])
+            assert np.linalg.norm(o["u"][g] - ref.u[g]) <= error_bound(prob, f, o["u"][g], ref.u[g]), (shape, g)
+    srv.close()
