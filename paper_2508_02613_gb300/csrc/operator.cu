@@ -376,9 +376,28 @@ constexpr int kWarpsPerCta3d = 4;
 #ifndef JFFT_K3D_SEG
 #define JFFT_K3D_SEG 8
 #endif
+#ifndef JFFT_K3D_MINB64
+#define JFFT_K3D_MINB64 2
+#endif
+#ifndef JFFT_K3D_J64
+#define JFFT_K3D_J64 4
+#endif
+// separable marching kernel (k_apply_K3s): node rows per warp and plane segment
+#ifndef JFFT_K3S_J
+#define JFFT_K3S_J 4
+#endif
+#ifndef JFFT_K3S_SEG
+#define JFFT_K3S_SEG 8
+#endif
+#ifndef JFFT_USE_K3S
+#define JFFT_USE_K3S 1
+#endif
+
+// FP64 instances hold every value in two registers: two resident blocks per SM (255 registers).
+template <typename T> constexpr int k3d_min_blocks() { return sizeof(T) == 8 ? JFFT_K3D_MINB64 : JFFT_K3D_MINB; }
 
 template <typename T, int J, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, typename TE = T>
-__global__ void __launch_bounds__(32 * kWarpsPerCta3d, JFFT_K3D_MINB)
+__global__ void __launch_bounds__(32 * kWarpsPerCta3d, k3d_min_blocks<T>())
     k_apply_K3d(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
                 T* __restrict__ y, int64_t fstride, int seg, int groups2, int rowblocks,
                 const StrainShift* __restrict__ shifts, T sgn, double* __restrict__ partial,
@@ -502,6 +521,188 @@ static cudaError_t apply_K3d_t(const Grid& g, const ElemConstT<T>& ec, const TE*
   return cudaGetLastError();
 }
 
+// 3D operator, separable warp-marching form. The element transform of element_force
+// (corner values -> Walsh-Hadamard modes -> mode forces -> corner forces) is split by
+// axis so that the butterfly stages shared by neighbouring elements run once:
+//   forward: the plane stage (axis 0: u(e0+1) +- u(e0)) once per node, the row stage
+//   (axis 1) once per (row pair, column), the column stage (axis 2) per element with the
+//   right column's row-stage values from lane l + 1;
+//   backward: the column stage per element, the right column's half sent to lane l + 1
+//   and added there (the node-column sum), the row stage per (row pair, column), the
+//   node-row sum over the two element rows, then the plane stage once per node, whose
+//   e0 + 1 half is carried to the next plane step.
+// Lane l of warp w owns node column c = 30 w + l (columns wrap periodically); lanes 0..30
+// compute the elements whose corner columns are c and c + 1, lanes 1..30 write node
+// column c (stride 30: every element a warp needs has both columns inside the warp, no
+// halo loads). A warp covers node rows j0 .. j0 + J - 1 along axis 1 (element rows j0 - 1
+// .. j0 + J - 1) and marches planes e0 = L0 - 1 .. L0 + seg - 1 along axis 0; the values of
+// plane e0 + 1 stay in registers for the next step, so each node is loaded once per
+// segment. Same mode arithmetic as element_force (mode_forces, E scaling with the
+// force-free mode 0 left out, the optional strain shift), different association order.
+constexpr int kColsPerWarp3s = 30;
+
+template <typename T, int J, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, typename TE = T>
+__global__ void __launch_bounds__(32 * kWarpsPerCta3d, k3d_min_blocks<T>())
+    k_apply_K3s(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
+                T* __restrict__ y, int64_t fstride, int seg, int groups2, int rowblocks,
+                const StrainShift* __restrict__ shifts, T sgn, double* __restrict__ partial,
+                CgState* __restrict__ cg, StageCtl sc) {
+  const int b = blockIdx.z;
+  if (cg && cg[b].done) return;
+  StrainShift sh;
+  if (SHIFT) sh = shifts[b];
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int64_t N = g.N;
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * kWarpsPerCta3d + (threadIdx.x >> 5);
+  const bool active_warp = wid < groups2 * rowblocks;
+  const int g2 = active_warp ? wid % groups2 : 0;
+  const int j0 = active_warp ? (wid / groups2) * J : 0;
+  const int cu = g2 * kColsPerWarp3s + lane;  // column before wrapping
+  const int c = cu & (n2 - 1);
+  const bool writer = active_warp && lane >= 1 && lane <= kColsPerWarp3s && cu <= n2;
+  const T* xb = x + (int64_t)b * fstride;
+  T* yb = y + (int64_t)b * fstride;
+  const int L0 = blockIdx.y * seg;
+  constexpr int R = J + 2;  // node rows j0 - 1 .. j0 + J
+  T dot = T(0);
+  if (active_warp) {
+    int roff[R];  // offset of node row j0 - 1 + i within a plane, own column (a plane has < 2^31 nodes)
+#pragma unroll
+    for (int i = 0; i < R; ++i) roff[i] = ((j0 - 1 + i) & (n1 - 1)) * n2 + c;
+    T A[R][3];  // plane e0, own column
+    {
+      const int64_t pb = (int64_t)((L0 - 1) & (n0 - 1)) * n1 * n2;
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A[i][a] = HAS_X ? xb[a * N + pb + roff[i]] : T(0);
+    }
+    T carry[J][3];
+#pragma unroll
+    for (int i = 0; i < J; ++i)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) carry[i][a] = T(0);
+    for (int e0 = L0 - 1; e0 < L0 + seg; ++e0) {
+      const int64_t pb0 = (int64_t)(e0 & (n0 - 1)) * n1 * n2;
+      const int64_t pb1 = (int64_t)((e0 + 1) & (n0 - 1)) * n1 * n2;
+      // node row 0 of the sweep (j0 - 1): plane stage
+      T Sb[3], Db[3], Xb[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T v1 = HAS_X ? xb[a * N + pb1 + roff[0]] : T(0);
+        Sb[a] = v1 + A[0][a];
+        Db[a] = v1 - A[0][a];
+        Xb[a] = A[0][a];
+        A[0][a] = v1;
+      }
+      T racc[3][2];  // node row being summed: plane-stage modes (sum, difference)
+#pragma unroll
+      for (int k = 0; k <= J; ++k) {  // element row e1 = j0 - 1 + k: node rows k (bottom), k + 1 (top)
+        T St[3], Dt[3], Xt[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T v1 = HAS_X ? xb[a * N + pb1 + roff[k + 1]] : T(0);
+          St[a] = v1 + A[k + 1][a];
+          Dt[a] = v1 - A[k + 1][a];
+          Xt[a] = A[k + 1][a];
+          A[k + 1][a] = v1;
+        }
+        // row stage, then column stage with lane l + 1: modes W[a][m], m bits (axis0 4, axis1 2, axis2 1)
+        T W[3][8];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T v0 = St[a] + Sb[a], v2 = St[a] - Sb[a], v4 = Dt[a] + Db[a], v6 = Dt[a] - Db[a];
+          const T r0 = __shfl_down_sync(0xffffffffu, v0, 1), r2 = __shfl_down_sync(0xffffffffu, v2, 1);
+          const T r4 = __shfl_down_sync(0xffffffffu, v4, 1), r6 = __shfl_down_sync(0xffffffffu, v6, 1);
+          W[a][0] = r0 + v0; W[a][1] = r0 - v0;
+          W[a][2] = r2 + v2; W[a][3] = r2 - v2;
+          W[a][4] = r4 + v4; W[a][5] = r4 - v4;
+          W[a][6] = r6 + v6; W[a][7] = r6 - v6;
+        }
+        if (SHIFT) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) W[a][mbit<3>(bb)] += T(sh.s[a][bb]);
+        }
+        const int e1 = j0 - 1 + k;
+        const T Ee = HAS_E ? eload<T>(E, pb0 + (int64_t)(e1 & (n1 - 1)) * n2 + c) : e_uniform;
+        T F[3][8];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int m = 0; m < 8; ++m) F[a][m] = T(0);
+        mode_forces<3>(ec, W, F);
+        // backward: column stage (own half o2 = 0, right half o2 = 1 to lane l + 1), then row stage
+        T top[3][2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          T Q[4];  // modes over (axis0, axis1): index (m >> 1)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int m = 2 * q;
+            const T y0 = m == 0 ? T(0) : F[a][m] * Ee, y1 = F[a][m | 1] * Ee;
+            const T own = y0 - y1, right = y0 + y1;
+            Q[q] = own + __shfl_up_sync(0xffffffffu, right, 1);
+          }
+          // row stage: bottom node row (o1 = 0) and top node row (o1 = 1), per plane mode
+          const T bot0 = Q[0] - Q[1], top0 = Q[0] + Q[1];   // plane-sum mode (axis0 bit clear)
+          const T bot1 = Q[2] - Q[3], top1 = Q[2] + Q[3];   // plane-difference mode
+          top[a][0] = top0;
+          top[a][1] = top1;
+          if (k >= 1) {
+            // node row j0 - 1 + k complete: plane stage -> planes e0 (o0 = 0) and e0 + 1 (o0 = 1)
+            const T t0 = racc[a][0] + bot0, t1 = racc[a][1] + bot1;
+            const T f0 = t0 - t1, f1 = t0 + t1;
+            if (e0 >= L0 && writer) {
+              const T sum = carry[k - 1][a] + f0;
+              const T q = SHIFT ? sgn * sum : sum;
+              yb[a * N + pb0 + roff[k]] = q;
+              if (DOT == 1) dot += Xb[a] * q;
+              if (DOT == 2) dot += q * q;
+            }
+            carry[k - 1][a] = f1;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          racc[a][0] = top[a][0];
+          racc[a][1] = top[a][1];
+          Sb[a] = St[a];
+          Db[a] = Dt[a];
+          Xb[a] = Xt[a];
+        }
+      }
+    }
+  }
+  if (DOT) {
+    const double s = block_sum((double)dot);
+    if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
+    fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x * gridDim.y);
+  }
+}
+
+template <typename T, int J, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false, typename TE = T>
+static cudaError_t apply_K3s_t(const Grid& g, const ElemConstT<T>& ec, const TE* E, T e_uniform, const T* x, T* y, int nb,
+                               int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
+                               StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
+  const int groups2 = (g.n[2] + kColsPerWarp3s - 1) / kColsPerWarp3s;
+  const int rowblocks = g.n[1] / J;
+  const int warps = groups2 * rowblocks;
+  const int ctas_x = (warps + kWarpsPerCta3d - 1) / kWarpsPerCta3d;
+  int seg = std::min(g.n[0], g.tune[1] > 0 ? g.tune[1] : JFFT_K3S_SEG);
+  while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
+  dim3 grid(ctas_x, g.n[0] / seg, nb);
+  const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
+                     : DOT == 1 ? "apply_K"
+                     : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
+  JFFT_K(name, st, k_apply_K3s<T, J, DOT, HAS_E, HAS_X, SHIFT, TE><<<grid, 32 * kWarpsPerCta3d, 0, st>>>(
+                       g, ec, E, e_uniform, x, y, fstride, seg, groups2, rowblocks, shifts, sgn, partial, cg, sc));
+  if (nparts) *nparts = grid.x * grid.y;
+  return cudaGetLastError();
+}
+
 template <int D> static MarchGeom march_geom(const Grid& g) {
   MarchGeom m;
   if (D == 2) {
@@ -539,6 +740,11 @@ static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const TE* E
   return cudaGetLastError();
 }
 
+#ifndef JFFT_WARP3D_F64
+#define JFFT_WARP3D_F64 1
+#endif
+constexpr bool kUseWarp3dF64 = JFFT_WARP3D_F64 != 0;
+
 template <int D>
 static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
                              double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, int dot_mode,
@@ -559,6 +765,19 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
     }
   }
   if (ec.elem != 0) return cudaErrorInvalidValue;  // P1 voxels run only on the 2D warp kernel
+  // 3D FP64: the warp-marching kernel on large grids (512^3: 80 against 89 ms per operator
+  // application), the shared-memory tile kernel below that (128^3: 7.8 against 8.2 ms)
+  if (D == 3 && g.n[1] >= JFFT_K3D_J64 && kUseWarp3dF64 && g.N >= (int64_t(1) << 24)) {
+    if (hx && he && !sh && dot_mode == 1)
+      return apply_K3d_t<double, JFFT_K3D_J64, 1, true, true, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
+                                                                     nparts, cg, st, sc);
+    if (hx && he && !sh && dot_mode == 0)
+      return apply_K3d_t<double, JFFT_K3D_J64, 0, true, true, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
+                                                                     nparts, cg, st, sc);
+    if (hx && he && sh && dot_mode == 2)
+      return apply_K3d_t<double, JFFT_K3D_J64, 2, true, true, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
+                                                                    nparts, cg, st, sc, shifts, sgn);
+  }
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
     return apply_K_t<double, D, DOT, HX, HE, SH>(g, ec, E, e_uniform, x, y, nb, fstride, shifts, sgn, partial, nparts, cg, st, sc);
@@ -633,6 +852,13 @@ static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, con
     if (dot_mode == 1)
       return apply_K2d_t<float, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
     return apply_K2d_t<float, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
+  }
+  if (JFFT_USE_K3S && g.n[1] >= JFFT_K3S_J) {
+    if (dot_mode == 1)
+      return apply_K3s_t<float, JFFT_K3S_J, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
+                                                                      cg, st, sc);
+    return apply_K3s_t<float, JFFT_K3S_J, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
+                                                                    cg, st, sc);
   }
   if (g.n[1] >= JFFT_K3D_J) {
     if (dot_mode == 1)

@@ -45,7 +45,8 @@ def error_bound(prob, f, u_a, u_b):
     return (ra + rb) / lam_min
 
 
-@pytest.mark.parametrize("shape", [(8, 16), (64, 512), (8, 4, 16), (16, 16, 64)])
+@pytest.mark.parametrize("shape", [(8, 16), (64, 512), (8, 4, 16), (16, 16, 64), (8, 16, 64), (4, 64, 32),
+                                   (16, 8, 128), (8, 32, 4)])
 def test_fp32_operator_and_preconditioners(shape):
     d = len(shape)
     rho = smooth_density(shape, 8, 3.0, 1)
