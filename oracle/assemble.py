@@ -54,13 +54,16 @@ def assemble_K(n, E: np.ndarray, C: np.ndarray, element: str = "q1") -> sp.csr_m
 
 
 def assemble_rhs(n, E: np.ndarray, C: np.ndarray, eps_bar: np.ndarray, element: str = "q1") -> np.ndarray:
-    """f = -sum_e E_e P_e^T b(eps_bar), b = sum_q w_q B_q^T C eps_bar. Shape [d, *n]."""
+    """f = -sum_e E_e P_e^T b(eps_bar), b = sum_q w_q B_q^T C eps_bar. Shape [d, *n], in the
+    floating-point type of E and C (at least FP64)."""
     n = tuple(int(k) for k in n)
     d = len(n)
-    b = fe.element_strain_load(d, grid_spacing(n), C, np.asarray(eps_bar, dtype=np.float64), element)
+    dtype = np.result_type(np.asarray(E).dtype, np.asarray(C).dtype, np.float64).type
+    b = fe.element_strain_load(d, grid_spacing(n), np.asarray(C, dtype=dtype), np.asarray(eps_bar, dtype=dtype),
+                               element)
     g = element_dofs(n)
-    vals = -(np.asarray(E, dtype=np.float64).reshape(-1)[:, None] * b[None, :])
-    f = np.zeros(d * int(np.prod(n)))
+    vals = -(np.asarray(E, dtype=dtype).reshape(-1)[:, None] * b[None, :])
+    f = np.zeros(d * int(np.prod(n)), dtype=dtype)
     np.add.at(f, g.reshape(-1), vals.reshape(-1))
     return f.reshape((d,) + n)
 

@@ -13,6 +13,25 @@ def diag_assembled(K: sp.csr_matrix, shape) -> np.ndarray:
     return K.diagonal().reshape(shape)
 
 
+def diag_matrix_free(n, E: np.ndarray, C: np.ndarray, element: str = "q1") -> np.ndarray:
+    """diag(K) without assembly: node I, component alpha collects E_e A[(alpha, o), (alpha, o)]
+    from each of the 2^d voxels e = I - o that have I at their corner o (A the unit
+    element matrix). In the floating-point type of E and C (the extended-precision oracle
+    derives its Jacobi scaling this way). Shape [d, *n]."""
+    from . import assemble, fe
+    n = tuple(int(k) for k in n)
+    d = len(n)
+    A = fe.element_matrix(d, assemble.grid_spacing(n), C, element)
+    E = np.asarray(E).astype(A.dtype)
+    nc = 2 ** d
+    out = np.zeros((d,) + n, dtype=A.dtype)
+    for ci, o in enumerate(fe.corners(d)):
+        Eo = np.roll(E, tuple(o), tuple(range(d)))   # E of the voxel with corner o at each node
+        for a in range(d):
+            out[a] += Eo * A[a * nc + ci, a * nc + ci]
+    return out
+
+
 def diag_alg2(apply_K, d: int, n) -> tuple[np.ndarray, int]:
     """Alg. 2: diag(K) from d 2^d operator applications to impulse combs.
 
@@ -50,4 +69,4 @@ def jacobi_half(diag: np.ndarray, replacement: float = 1.0) -> np.ndarray:
     """J^(1/2) = diag(K)^(-1/2), with zero entries replaced by ``replacement`` first."""
     dd = diag.copy()
     dd[dd == 0.0] = replacement
-    return 1.0 / np.sqrt(dd)
+    return 1 / np.sqrt(dd)

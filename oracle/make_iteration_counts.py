@@ -7,23 +7,30 @@ Green-Jacobi, relative residual 1e-8 (Sec. 4 "Termination criteria", relative fo
 Each solve runs the oracle's textbook PCG (matrix-free K, support-form Alg. 1) to
 completion under several rounding variants of the same arithmetic:
 
-  fp64/blas        FP64, inner products by numpy.dot
-  fp64/sequential  FP64, inner products summed left to right
-  extended/blas    every vector, scalar, operator and transform in numpy.longdouble
-                   (64-bit significand on x86; Green-Jacobi only)
+  fp64/blas                 FP64, inner products by numpy.dot
+  fp64/sequential           FP64, inner products summed left to right
+  extended/blas             everything derived from the FP64 inputs (E, nu) in
+                            numpy.longdouble (64-bit significand on x86): C, element
+                            matrix, symbol, diagonal, J^(1/2), right-hand side, and the
+                            whole iteration (Green-Jacobi only)
+  extended_iteration/blas   the FP64 setup arrays and right-hand side, the iteration in
+                            numpy.longdouble (Green-Jacobi only)
 
-Green-Jacobi PCG at this size amplifies rounding-level differences by roughly six per
-iteration once its first Ritz values settle (about iteration 12), so its count depends
-on the rounding: the less accurate the arithmetic, the later it stops. The extended
-run is the least delayed; the FP64 sequential run the most. The GPU parity test takes
-the range over the variants, widened by one, as the window for a correct
-implementation of the same iteration. Green PCG does not amplify rounding (its
+Green-Jacobi PCG at this size amplifies differences of rounding size by roughly six
+per iteration once its first Ritz values settle (about iteration 12), so its count is
+set by rounding: by the arithmetic (the less accurate, the later it stops) and even by
+the last bit of the setup arrays (the two extended variants differ only by rounding
+C, the symbol and J^(1/2) to FP64 and stop up to four iterations apart). The GPU
+parity test takes the range over the variants, widened by one, as the window for a
+correct implementation of the same iteration. Green PCG does not amplify rounding (its
 variants agree to ~1e-13 over the whole run) and is recorded in FP64 only.
 
 Output: oracle/data/iters_2d_1024.json, read by the GPU count test and by the
 CPU-baseline and reference legs of bench.py to scale their bounded samples.
 
-    python -m oracle.make_iteration_counts [--workers 8]
+    python -m oracle.make_iteration_counts [--workers 8] [--only fp64|extended|extended_iteration ...]
+
+``--only`` recomputes the rows of the named precisions and keeps the file's other rows.
 """
 
 from __future__ import annotations
@@ -50,12 +57,15 @@ def _one(args):
     contrast, pc, load, precision, order = args
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
-    from oracle import assemble, material, pcg, solve
+    from oracle import assemble, fe, material, pcg, solve
     from synthetic import smooth_density
     rho = smooth_density(SHAPE, 16, 8.0, 0)
     E = material.young_from_density(rho, 1.0 / contrast, 1.0, 2.0)
     prob = solve.setup(SHAPE, E, 0.3, precision=precision)
-    f = assemble.assemble_rhs(SHAPE, E, prob.C, np.eye(3)[load]).astype(prob.E.dtype)
+    if precision == "extended":
+        f = assemble.assemble_rhs(SHAPE, prob.E, prob.C, np.eye(3)[load])   # derived in extended precision
+    else:
+        f = assemble.assemble_rhs(SHAPE, E, fe.C_unit(2, 0.3), np.eye(3)[load]).astype(prob.E.dtype)
     t = time.time()
     res = pcg.pcg(prob.apply_K, prob.minv(pc), f, TOL, 100000, "rel", order)
     return {"contrast": contrast, "precond": pc, "load": load, "precision": precision, "dot": order,
@@ -71,8 +81,9 @@ def jobs():
                 out.append((c, pc, g, "fp64", "sequential"))
                 if pc == "green_jacobi":
                     out.append((c, pc, g, "extended", "blas"))
+                    out.append((c, pc, g, "extended_iteration", "blas"))
     # longest first: Green at high contrast runs thousands of iterations
-    cost = lambda j: (j[1] == "green") * j[0] + (j[3] == "extended") * 5e3  # noqa: E731
+    cost = lambda j: (j[1] == "green") * j[0] + (j[3] != "fp64") * 5e3  # noqa: E731
     return sorted(out, key=cost, reverse=True)
 
 
@@ -80,10 +91,17 @@ def main():
     workers = 8
     if "--workers" in sys.argv:
         workers = int(sys.argv[sys.argv.index("--workers") + 1])
+    only = set()
+    if "--only" in sys.argv:
+        only = set(sys.argv[sys.argv.index("--only") + 1:])
+    todo = [j for j in jobs() if not only or j[3] in only]
+    kept = []
+    if only and os.path.exists(OUT):
+        kept = [r for r in json.load(open(OUT))["solves"] if r["precision"] not in only]
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     with mp.get_context("spawn").Pool(workers) as pool:
-        rows = pool.map(_one, jobs(), chunksize=1)
+        rows = kept + pool.map(_one, todo, chunksize=1)
     rows.sort(key=lambda r: (r["contrast"], r["precond"], r["load"], r["precision"], r["dot"]))
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     with open(OUT, "w") as fh:
@@ -92,7 +110,9 @@ def main():
                    "oracle": "matrix-free K on corner differences, Alg. 1 over the impulse responses' support",
                    "variants": {"fp64/blas": "FP64, numpy.dot inner products",
                                 "fp64/sequential": "FP64, inner products summed left to right",
-                                "extended/blas": "numpy.longdouble throughout (x86: 64-bit significand)"},
+                                "extended/blas": "setup and iteration in numpy.longdouble (x86: 64-bit significand) "
+                                                 "from the FP64 inputs",
+                                "extended_iteration/blas": "FP64 setup arrays, iteration in numpy.longdouble"},
                    "solves": rows}, fh, indent=1)
     print(OUT)
 

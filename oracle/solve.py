@@ -74,29 +74,39 @@ def setup(n, E: np.ndarray, nu: float, C_ref: np.ndarray | None = None,
     the first and ~eps/theta^2 for the second (theta the lowest grid frequency).
     ``symbol``: how step 2 of Alg. 1 transforms the impulse responses, "support"
     (default, green.support_transform) or "fft" (the full FFT, real and even part).
-    ``precision``: "fp64", or "extended" (numpy.longdouble, 64-bit significand on x86)
-    for the matrix-free operator, the symbol, J^(1/2) and every PCG vector and scalar
-    (the inputs E, C and the diagonal are the FP64 values); it measures how far FP64
-    rounding moves the PCG iteration counts."""
+    ``precision``: "fp64"; "extended" (numpy.longdouble, 64-bit significand on x86) for
+    everything derived from the FP64 inputs E and nu: C, the element matrix, the
+    reference material, the Alg. 1 symbol, the diagonal (matrix-free, jacobi.
+    diag_matrix_free), J^(1/2), and every PCG vector and scalar; or "extended_iteration",
+    the FP64 setup arrays (C, symbol, J^(1/2)) cast to numpy.longdouble and only the
+    iteration in extended precision. Both measure how far FP64 rounding moves the PCG
+    iteration counts."""
     if operator not in ("matrix_free", "assembled"):
         raise ValueError(operator)
-    if precision not in ("fp64", "extended"):
+    if precision not in ("fp64", "extended", "extended_iteration"):
         raise ValueError(precision)
-    if precision == "extended" and (operator != "matrix_free" or symbol != "support"):
+    if precision != "fp64" and (operator != "matrix_free" or symbol != "support"):
         raise ValueError("extended precision needs the matrix-free operator and the support-form symbol")
-    dt = np.longdouble if precision == "extended" else np.float64
     n = tuple(int(k) for k in n)
     d = len(n)
     E = np.asarray(E, dtype=np.float64).reshape(n)
     C = fe.C_unit(d, nu)
     K = assemble.assemble_K(n, E, C, element)
+    diag = jacobi.diag_assembled(K, (d,) + n)
+    if precision == "extended":
+        ld = np.longdouble
+        E_l, C_l = E.astype(ld), fe.C_unit(d, nu, ld)
+        C_ref_l = E_l.mean() * C_l if C_ref is None else np.asarray(C_ref).astype(ld)
+        _, G_hat = green.green_symbol(n, C_ref_l, element=element, transform=symbol, dtype=ld)
+        J_half = jacobi.jacobi_half(jacobi.diag_matrix_free(n, E_l, C_l, element), ld(void_replacement))
+        return CellProblem(n, E_l, nu, C_l, K, G_hat, diag, J_half, element, operator)
     if C_ref is None:
         C_ref = float(E.mean()) * C
-    _, G_hat = green.green_symbol(n, C_ref, element=element, transform=symbol, dtype=dt)
-    diag = jacobi.diag_assembled(K, (d,) + n)
+    _, G_hat = green.green_symbol(n, C_ref, element=element, transform=symbol)
     J_half = jacobi.jacobi_half(diag, void_replacement)
-    if dt is not np.float64:
-        E, C, J_half = E.astype(dt), C.astype(dt), J_half.astype(dt)
+    if precision == "extended_iteration":
+        ld = np.longdouble
+        E, C, J_half, G_hat = E.astype(ld), C.astype(ld), J_half.astype(ld), G_hat.astype(ld)
     return CellProblem(n, E, nu, C, K, G_hat, diag, J_half, element, operator)
 
 

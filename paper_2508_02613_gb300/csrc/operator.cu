@@ -352,174 +352,25 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const TE*
   return cudaGetLastError();
 }
 
-// 3D operator, warp-marching form. Lane l owns node column c = c0 + l along the
-// contiguous axis 2 (warps overlap by one column, stride 31, as in 2D); a warp
-// covers J consecutive node rows j0 .. j0 + J - 1 along axis 1 and walks `seg` planes
-// along axis 0. At plane step e0 it sweeps the element rows e1 = j0 - 1 .. j0 + J - 1
-// (the first one is the previous warp's last, computed again). For element (e0, e1, c)
-// the lane holds node rows e1 and e1 + 1 of planes e0 and e0 + 1 of its own column;
-// column c + 1 arrives from lane l + 1 by a shuffle (lane 31 loads it itself) and
-// the corner forces of column c + 1 go back to lane l + 1 by a shuffle. Forces on
-// plane e0 are summed while the sweep passes (a node row is complete after element
-// rows e1 - 1 and e1); forces on plane e0 + 1 are kept per node row for the next
-// plane step. No shared memory, no block barrier.
+// Launch shape of the 3D marching kernel below (measured on GB300 at 128^3 x 6 loads and
+// 512^3: J = 4 node rows per warp, four resident blocks per SM in FP32 and two in FP64,
+// 8-plane segments; the per-node summation order does not depend on these).
 constexpr int kWarpsPerCta3d = 4;
-// Launch shape (measured at 128^3 x 6 loads and 256^3: J = 4 node rows per warp, four
-// resident blocks per SM, 8-plane segments was the fastest of J 2..8, 1..4 blocks, 8 / 16
-// planes; the per-node summation order does not depend on these).
-#ifndef JFFT_K3D_J
-#define JFFT_K3D_J 4
-#endif
-#ifndef JFFT_K3D_MINB
-#define JFFT_K3D_MINB 4
-#endif
-#ifndef JFFT_K3D_SEG
-#define JFFT_K3D_SEG 8
-#endif
-#ifndef JFFT_K3D_MINB64
-#define JFFT_K3D_MINB64 2
-#endif
-#ifndef JFFT_K3D_J64
-#define JFFT_K3D_J64 4
-#endif
-// separable marching kernel (k_apply_K3s): node rows per warp and plane segment
 #ifndef JFFT_K3S_J
 #define JFFT_K3S_J 4
 #endif
 #ifndef JFFT_K3S_SEG
 #define JFFT_K3S_SEG 8
 #endif
-#ifndef JFFT_USE_K3S
-#define JFFT_USE_K3S 1
+#ifndef JFFT_K3S_MINB
+#define JFFT_K3S_MINB 4
+#endif
+#ifndef JFFT_K3S_MINB64
+#define JFFT_K3S_MINB64 2
 #endif
 
 // FP64 instances hold every value in two registers: two resident blocks per SM (255 registers).
-template <typename T> constexpr int k3d_min_blocks() { return sizeof(T) == 8 ? JFFT_K3D_MINB64 : JFFT_K3D_MINB; }
-
-template <typename T, int J, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, typename TE = T>
-__global__ void __launch_bounds__(32 * kWarpsPerCta3d, k3d_min_blocks<T>())
-    k_apply_K3d(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
-                T* __restrict__ y, int64_t fstride, int seg, int groups2, int rowblocks,
-                const StrainShift* __restrict__ shifts, T sgn, double* __restrict__ partial,
-                CgState* __restrict__ cg, StageCtl sc) {
-  const int b = blockIdx.z;
-  if (cg && cg[b].done) return;
-  StrainShift sh;
-  if (SHIFT) sh = shifts[b];
-  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-  const int64_t N = g.N;
-  const int lane = threadIdx.x & 31;
-  const int wid = blockIdx.x * kWarpsPerCta3d + (threadIdx.x >> 5);
-  const bool active_warp = wid < groups2 * rowblocks;
-  const int g2 = active_warp ? wid % groups2 : 0;
-  const int j0 = active_warp ? (wid / groups2) * J : 0;
-  const int o = g2 * kWarpStride + lane;
-  const int c = o & (n2 - 1), cr = (o + 1) & (n2 - 1);
-  const bool writer = active_warp && lane >= 1 && o <= n2;
-  const T* xb = x + (int64_t)b * fstride;
-  T* yb = y + (int64_t)b * fstride;
-  const int L0 = blockIdx.y * seg;
-  T dot = T(0);
-  if (active_warp) {
-    T carry[J][3];
-#pragma unroll
-    for (int r = 0; r < J; ++r)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) carry[r][a] = T(0);
-    for (int e0 = L0 - 1; e0 < L0 + seg; ++e0) {
-      const int p0 = e0 & (n0 - 1), p1 = (e0 + 1) & (n0 - 1);
-      const int64_t b0 = (int64_t)p0 * n1, b1 = (int64_t)p1 * n1;
-      // node row e1 = j0 - 1 of both planes (own column and column c + 1)
-      T lo0[3], lo1[3], rlo0[3], rlo1[3];
-      {
-        const int r = (j0 - 1) & (n1 - 1);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          lo0[a] = HAS_X ? xb[a * N + (b0 + r) * n2 + c] : T(0);
-          lo1[a] = HAS_X ? xb[a * N + (b1 + r) * n2 + c] : T(0);
-          const T h0 = (HAS_X && lane == 31) ? xb[a * N + (b0 + r) * n2 + cr] : T(0);
-          const T h1 = (HAS_X && lane == 31) ? xb[a * N + (b1 + r) * n2 + cr] : T(0);
-          rlo0[a] = __shfl_down_sync(0xffffffffu, lo0[a], 1);
-          rlo1[a] = __shfl_down_sync(0xffffffffu, lo1[a], 1);
-          if (lane == 31) { rlo0[a] = h0; rlo1[a] = h1; }
-        }
-      }
-      T pacc[3] = {T(0), T(0), T(0)}, qacc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int k = 0; k <= J; ++k) {
-        const int e1 = j0 - 1 + k;
-        const int r1 = (e1 + 1) & (n1 - 1);
-        T hi0[3], hi1[3], rhi0[3], rhi1[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          hi0[a] = HAS_X ? xb[a * N + (b0 + r1) * n2 + c] : T(0);
-          hi1[a] = HAS_X ? xb[a * N + (b1 + r1) * n2 + c] : T(0);
-          const T h0 = (HAS_X && lane == 31) ? xb[a * N + (b0 + r1) * n2 + cr] : T(0);
-          const T h1 = (HAS_X && lane == 31) ? xb[a * N + (b1 + r1) * n2 + cr] : T(0);
-          rhi0[a] = __shfl_down_sync(0xffffffffu, hi0[a], 1);
-          rhi1[a] = __shfl_down_sync(0xffffffffu, hi1[a], 1);
-          if (lane == 31) { rhi0[a] = h0; rhi1[a] = h1; }
-        }
-        const T Ee = HAS_E ? eload<T>(E, (b0 + (e1 & (n1 - 1))) * n2 + c) : e_uniform;
-        // corner index o0 * 4 + o1 * 2 + o2 (axis 0 is the highest bit)
-        T u[3][8];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          u[a][0] = lo0[a]; u[a][1] = rlo0[a]; u[a][2] = hi0[a]; u[a][3] = rhi0[a];
-          u[a][4] = lo1[a]; u[a][5] = rlo1[a]; u[a][6] = hi1[a]; u[a][7] = rhi1[a];
-        }
-        element_force<3, T, SHIFT>(ec, &sh, u, Ee);
-        const bool out_row = k >= 1;   // node row e1 = j0 + k - 1 is one of this warp's rows
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          // own-column totals t(o0, o1) = f(o0, o1, 0) + f(o0, o1, 1) of column c - 1
-          const T t00 = u[a][0] + __shfl_up_sync(0xffffffffu, u[a][1], 1);
-          const T t01 = u[a][2] + __shfl_up_sync(0xffffffffu, u[a][3], 1);
-          const T t10 = u[a][4] + __shfl_up_sync(0xffffffffu, u[a][5], 1);
-          const T t11 = u[a][6] + __shfl_up_sync(0xffffffffu, u[a][7], 1);
-          if (out_row) {
-            if (e0 >= L0 && writer) {
-              const T sum = carry[k - 1][a] + pacc[a] + t00;
-              const T q = SHIFT ? sgn * sum : sum;  // sgn is 1 for the forms without a strain shift
-              yb[a * N + (b0 + (e1 & (n1 - 1))) * n2 + (o & (n2 - 1))] = q;
-              if (DOT == 1) dot += lo0[a] * q;
-              if (DOT == 2) dot += q * q;
-            }
-            carry[k - 1][a] = qacc[a] + t10;
-          }
-          pacc[a] = t01;
-          qacc[a] = t11;
-          lo0[a] = hi0[a]; lo1[a] = hi1[a]; rlo0[a] = rhi0[a]; rlo1[a] = rhi1[a];
-        }
-      }
-    }
-  }
-  if (DOT) {
-    const double s = block_sum((double)dot);
-    if (threadIdx.x == 0) partial[(int64_t)b * kMaxPartials + blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
-    fused_stage_tail(sc, cg, b, partial + (int64_t)b * kMaxPartials, gridDim.x * gridDim.y);
-  }
-}
-
-template <typename T, int J, int DOT, bool HAS_E, bool HAS_X = true, bool SHIFT = false, typename TE = T>
-static cudaError_t apply_K3d_t(const Grid& g, const ElemConstT<T>& ec, const TE* E, T e_uniform, const T* x, T* y, int nb,
-                               int64_t fstride, double* partial, int* nparts, CgState* cg, cudaStream_t st,
-                               StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
-  const int groups2 = (g.n[2] + kWarpStride - 1) / kWarpStride;
-  const int rowblocks = g.n[1] / J;
-  const int warps = groups2 * rowblocks;
-  const int ctas_x = (warps + kWarpsPerCta3d - 1) / kWarpsPerCta3d;
-  int seg = std::min(g.n[0], g.tune[1] > 0 ? g.tune[1] : JFFT_K3D_SEG);
-  while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
-  dim3 grid(ctas_x, g.n[0] / seg, nb);
-  const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
-                     : DOT == 1 ? "apply_K"
-                     : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
-  JFFT_K(name, st, k_apply_K3d<T, J, DOT, HAS_E, HAS_X, SHIFT, TE><<<grid, 32 * kWarpsPerCta3d, 0, st>>>(
-                       g, ec, E, e_uniform, x, y, fstride, seg, groups2, rowblocks, shifts, sgn, partial, cg, sc));
-  if (nparts) *nparts = grid.x * grid.y;
-  return cudaGetLastError();
-}
+template <typename T> constexpr int k3d_min_blocks() { return sizeof(T) == 8 ? JFFT_K3S_MINB64 : JFFT_K3S_MINB; }
 
 // 3D operator, separable warp-marching form. The element transform of element_force
 // (corner values -> Walsh-Hadamard modes -> mode forces -> corner forces) is split by
@@ -740,11 +591,6 @@ static cudaError_t apply_K_t(const Grid& g, const ElemConstT<T>& ec, const TE* E
   return cudaGetLastError();
 }
 
-#ifndef JFFT_WARP3D_F64
-#define JFFT_WARP3D_F64 1
-#endif
-constexpr bool kUseWarp3dF64 = JFFT_WARP3D_F64 != 0;
-
 template <int D>
 static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E, double e_uniform, const double* x,
                              double* y, int nb, int64_t fstride, const StrainShift* shifts, double sgn, int dot_mode,
@@ -765,18 +611,19 @@ static cudaError_t apply_K_d(const Grid& g, const ElemConst& ec, const double* E
     }
   }
   if (ec.elem != 0) return cudaErrorInvalidValue;  // P1 voxels run only on the 2D warp kernel
-  // 3D FP64: the warp-marching kernel on large grids (512^3: 80 against 89 ms per operator
-  // application), the shared-memory tile kernel below that (128^3: 7.8 against 8.2 ms)
-  if (D == 3 && g.n[1] >= JFFT_K3D_J64 && kUseWarp3dF64 && g.N >= (int64_t(1) << 24)) {
+  // 3D FP64: the separable marching kernel (128^3: 6.7 against 7.8 ms per operator
+  // application for the shared-memory tile kernel below, 512^3: 70 against 89 ms); the tile
+  // kernel keeps the grids with fewer than JFFT_K3S_J rows and the right-hand side form
+  if (D == 3 && g.n[1] >= JFFT_K3S_J) {
     if (hx && he && !sh && dot_mode == 1)
-      return apply_K3d_t<double, JFFT_K3D_J64, 1, true, true, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
-                                                                     nparts, cg, st, sc);
+      return apply_K3s_t<double, JFFT_K3S_J, 1, true, true, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
+                                                                   nparts, cg, st, sc);
     if (hx && he && !sh && dot_mode == 0)
-      return apply_K3d_t<double, JFFT_K3D_J64, 0, true, true, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
-                                                                     nparts, cg, st, sc);
+      return apply_K3s_t<double, JFFT_K3S_J, 0, true, true, false>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
+                                                                   nparts, cg, st, sc);
     if (hx && he && sh && dot_mode == 2)
-      return apply_K3d_t<double, JFFT_K3D_J64, 2, true, true, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
-                                                                    nparts, cg, st, sc, shifts, sgn);
+      return apply_K3s_t<double, JFFT_K3S_J, 2, true, true, true>(g, ec, E, e_uniform, x, y, nb, fstride, partial,
+                                                                  nparts, cg, st, sc, shifts, sgn);
   }
 #define JFFT_AK(DOT, HX, HE, SH) \
   if (dot_mode == DOT && hx == HX && he == HE && sh == SH) \
@@ -853,18 +700,11 @@ static cudaError_t apply_K_f32_d(const Grid& g, const ElemConstT<float>& ec, con
       return apply_K2d_t<float, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
     return apply_K2d_t<float, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts, cg, st, sc);
   }
-  if (JFFT_USE_K3S && g.n[1] >= JFFT_K3S_J) {
+  if (g.n[1] >= JFFT_K3S_J) {
     if (dot_mode == 1)
       return apply_K3s_t<float, JFFT_K3S_J, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
                                                                       cg, st, sc);
     return apply_K3s_t<float, JFFT_K3S_J, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
-                                                                    cg, st, sc);
-  }
-  if (g.n[1] >= JFFT_K3D_J) {
-    if (dot_mode == 1)
-      return apply_K3d_t<float, JFFT_K3D_J, 1, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
-                                                                      cg, st, sc);
-    return apply_K3d_t<float, JFFT_K3D_J, 0, true, true, false, TE>(g, ec, E, 0.f, x, y, nb, fstride, partial, nparts,
                                                                     cg, st, sc);
   }
   if (dot_mode == 1)

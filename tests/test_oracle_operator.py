@@ -327,3 +327,32 @@ def test_matrix_free_operator_accuracy_on_smooth_fields():
     asm = assemble.apply(assemble.assemble_K(shape, E, C), x)
     assert float(np.abs(mf - ref).max()) <= 1e-13 * scale
     assert float(np.abs(asm - ref).max()) > 1e-12 * scale
+
+
+@pytest.mark.parametrize("shape,element", [((8, 16), "q1"), ((4, 8, 4), "q1"), ((8, 8), "p1")])
+def test_matrix_free_diagonal_equals_assembled(shape, element):
+    d = len(shape)
+    E = np.random.default_rng(5).uniform(0.1, 1.0, shape)
+    C = fe.C_unit(d, 0.3)
+    want = jacobi.diag_assembled(assemble.assemble_K(shape, E, C, element), (d,) + shape)
+    got = jacobi.diag_matrix_free(shape, E, C, element)
+    assert np.abs(got - want).max() <= 1e-15 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("shape", [(16, 32), (8, 8, 8)])
+def test_extended_setup_agrees_with_fp64_to_rounding(shape):
+    """The extended-precision oracle derives C, the element matrix, the symbol and J^(1/2)
+    from the FP64 inputs in numpy.longdouble: equal to the FP64 setup to a few FP64 ulps."""
+    if np.finfo(np.longdouble).eps > 1e-18:
+        pytest.skip("no extended precision type on this platform")
+    d = len(shape)
+    E = material.young_from_density(smooth_density(shape, 8, 3.0, 2), 1e-3, 1.0, 2.0)
+    a = solve.setup(shape, E, 0.3)
+    b = solve.setup(shape, E, 0.3, precision="extended")
+    assert b.G_hat.dtype == np.longdouble and b.J_half.dtype == np.longdouble
+    assert float(np.abs(b.C - a.C).max()) <= 4e-16 * np.abs(a.C).max()
+    assert float(np.abs(b.G_hat - a.G_hat).max()) <= 1e-14 * np.abs(a.G_hat).max()
+    assert float(np.abs(b.J_half - a.J_half).max()) <= 4e-16 * np.abs(a.J_half).max()
+    A64 = fe.element_matrix(d, assemble.grid_spacing(shape), a.C)
+    Ald = fe.element_matrix(d, assemble.grid_spacing(shape), b.C)
+    assert Ald.dtype == np.longdouble and float(np.abs(Ald - A64).max()) <= 1e-15 * np.abs(A64).max()

@@ -159,3 +159,21 @@ def test_filtered_inclusion_trend():
     assert its[8]["green_jacobi"] < its[8]["green"]
     assert its[8]["green"] > 5 * its[0]["green"]
     assert its[8]["green_jacobi"] < its[0]["green_jacobi"]
+
+
+def test_extended_iterates_agree_with_fp64_before_amplification():
+    """The extended-precision PCG (setup and iteration) and the FP64 one agree to rounding
+    for the first iterations, at 64^2 Green-Jacobi, contrast 1e4."""
+    if np.finfo(np.longdouble).eps > 1e-18:
+        pytest.skip("no extended precision type on this platform")
+    shape = (64, 64)
+    E = material.young_from_density(smooth_density(shape, 16, 8.0, 0), 1e-4, 1.0, 2.0)
+    a = solve.setup(shape, E, 0.3)
+    b = solve.setup(shape, E, 0.3, precision="extended")
+    fa = assemble.assemble_rhs(shape, a.E, a.C, np.eye(3)[0])
+    fb = assemble.assemble_rhs(shape, b.E, b.C, np.eye(3)[0])
+    assert fb.dtype == np.longdouble
+    for k in (1, 5):
+        xa = pcg.pcg(a.apply_K, a.minv("green_jacobi"), fa, 0.0, k).x
+        xb = pcg.pcg(b.apply_K, b.minv("green_jacobi"), fb, 0.0, k).x.astype(np.float64)
+        assert np.linalg.norm(xa - xb) <= 1e-13 * np.linalg.norm(xa)
