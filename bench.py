@@ -188,6 +188,8 @@ def flops_per_unit(kernel, shape):
     real_fft = d * rows * 2.5 * n[-1] * math.log2(n[-1])
     if k == "fft_rows_real_fwd":
         return real_fft + d * N
+    if k == "fft_rows_real_fwd_xr":                # + x += alpha p, r -= alpha q, ||r||^2
+        return real_fft + d * N + 6 * d * N
     if k == "fft_cols_real_inv":
         return real_fft + 3 * d * N
     if k in ("fft_rows_cplx_fwd", "fft_cols_cplx_inv"):   # 3D middle axis
@@ -212,6 +214,8 @@ def traffic_bytes_per_unit(kernel, shape, material_bytes=None):
     table = {
         "fft_lines": 2 * d * F * 2 * s + F * ncmp * s,           # spectrum in + out, symbol table
         "fft_rows_real_fwd": d * N * s + d * F * 2 * s + N * s,   # r, spectrum, J^1/2 scale
+        # with the PCG update: x, r read + write, p, q, spectrum, J^1/2 scale
+        "fft_rows_real_fwd_xr": 6 * d * N * s + d * F * 2 * s + N * s,
         "fft_rows_cplx_fwd": 2 * d * F * 2 * s,                   # spectrum in + out
         "fft_cols_cplx_inv": 2 * d * F * 2 * s,
         "fft_cols_real_inv": d * F * 2 * s + 2 * d * N * s + N * s,   # spectrum, z, r (dot), scale

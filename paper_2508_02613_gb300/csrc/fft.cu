@@ -23,4 +23,11 @@ cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* 
   return green_precond_t<double>(g, p, r, z, nb, js, jacobi, partial, nparts, done, st, sc, jcs);
 }
 
+template <>
+cudaError_t launch_green_precond_xr<double>(const Grid& g, const FftPlanT<double>& p, double* x, double* r, const double* pv, const double* q,
+                                        double* z, int nb, const double* js, bool jacobi, double* partial, int* nparts,
+                                        CgState* cg, cudaStream_t st, StageCtl sc_rr, StageCtl sc, int64_t jcs) {
+  return green_precond_xr_t<double>(g, p, x, r, pv, q, z, nb, js, jacobi, partial, nparts, cg, st, sc_rr, sc, jcs);
+}
+
 }  // namespace jfft

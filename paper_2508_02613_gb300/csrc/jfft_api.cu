@@ -855,7 +855,9 @@ static jfft_status precond(jfft_solver* h, int pc, const double* r, double* z, i
 
 // One check_every-iteration chunk of the PCG loop: q = K p (alpha), x and r update
 // (residual test), z = M^-1 r (beta), p = z + beta p. Right-hand sides that are
-// done skip every kernel, so a chunk may run past convergence at no cost.
+// done skip every kernel, so a chunk may run past convergence at no cost. With the
+// Green preconditioners the x and r update runs inside the first FFT pass (the same
+// roundings of x and r; only the summation order of ||r||^2 differs).
 template <typename T>
 static cudaError_t pcg_chunk(jfft_solver* h, const Work<T>& w, int nb, int pc, double tol, int stop_mode, int chunk) {
   const Grid& g = h->g;
@@ -865,9 +867,17 @@ static cudaError_t pcg_chunk(jfft_solver* h, const Work<T>& w, int nb, int pc, d
   cudaError_t e;
   for (int c = 0; c < chunk; ++c) {
     if ((e = apply_op(h, w, w.p, w.q, nb, 1, &np, h->cg, stage(kStageAlpha))) != cudaSuccess) return e;
-    if ((e = launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st, stage(kStageRR))) != cudaSuccess)
-      return e;
-    if ((e = precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageBeta))) != cudaSuccess) return e;
+    if (pc == JFFT_PC_GREEN || pc == JFFT_PC_GREEN_JACOBI) {
+      if ((e = launch_green_precond_xr<T>(g, w.pl, w.x, w.r, w.p, w.q, w.z, nb, w.js, pc == JFFT_PC_GREEN_JACOBI,
+                                          h->partial, &np, h->cg, h->st, stage(kStageRR), stage(kStageBeta),
+                                          h->jcs)) != cudaSuccess)
+        return e;
+    } else {
+      if ((e = launch_cg_xr<T>(g, w.x, w.r, w.p, w.q, nb, fe, h->cg, h->partial, &np, h->st, stage(kStageRR))) !=
+          cudaSuccess)
+        return e;
+      if ((e = precond_op(h, w, pc, w.r, w.z, nb, h->cg, &np, stage(kStageBeta))) != cudaSuccess) return e;
+    }
     if ((e = launch_cg_p<T>(g, w.p, w.z, nb, fe, h->cg, h->st)) != cudaSuccess) return e;
   }
   return cudaSuccess;

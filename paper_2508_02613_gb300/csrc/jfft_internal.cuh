@@ -222,6 +222,14 @@ cudaError_t launch_green_precond(const Grid& g, const FftPlan& p, const double* 
 cudaError_t launch_green_precond_f32(const Grid& g, const FftPlanT<float>& p, const float* r, float* z, int nb,
                                      const float* js, bool jacobi, double* partial, int* nparts, CgState* cg,
                                      cudaStream_t st, StageCtl sc = no_stage(), int64_t jcs = 0);
+// The Green / Green-Jacobi preconditioner with the PCG update fused into its first pass:
+// x += alpha p, r -= alpha q (alpha read from cg), the residual stage sc_rr applied by
+// that pass's last block per right-hand side, then z = M^-1 r with the r.z partials and
+// the stage sc as above. Defined for T = double and float.
+template <typename T>
+cudaError_t launch_green_precond_xr(const Grid& g, const FftPlanT<T>& p, T* x, T* r, const T* pv, const T* q, T* z,
+                                    int nb, const T* js, bool jacobi, double* partial, int* nparts, CgState* cg,
+                                    cudaStream_t st, StageCtl sc_rr, StageCtl sc, int64_t jcs);
 // z = J r (J = diag(K)^-1 with the void rule) or z = r (identity), partial r.z.
 cudaError_t launch_jacobi_precond(const Grid& g, const double* r, double* z, int nb, int64_t stride, const double* js,
                                   bool identity, double* partial, int* nparts, CgState* cg, cudaStream_t st,

@@ -395,7 +395,7 @@ def test_deterministic_and_counts_launches():
     s.set_profiling(True)
     s.solve(mandel_unit_loads(2)[:1], 1e-8, "green_jacobi")
     prof = s.profile()
-    assert prof["apply_K"][0] > 0 and prof["fft_lines"][1] > 0
+    assert prof["apply_K"][0] > 0 and prof["fft_rows_real_fwd_xr"][0] > 0 and prof["fft_lines"][1] > 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
