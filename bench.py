@@ -64,6 +64,17 @@ CONFIGS_3D = {
                             "(32 Fourier modes, |k|<=12), E = 1/c + (1-1/c) rho^3, c = 1e6, nu 0.3; single load "
                             "eps_xy = 1 (Mandel sqrt(2) e_6); Green-Jacobi PCG to 1e-8 relative residual")},
 }
+# Profiling-only configurations (selectable with --only-3d, never part of the default run):
+# 256^3 with the 512^3 recipe and its single load, for ncu captures whose DRAM bytes scale
+# to 512^3 by the node count (x 8); a 512^3 capture would hold tens of GB on the device.
+PROFILE_CONFIGS_3D = {
+    "3d_256": {"shape": (256, 256, 256), "modes": 32, "kmax": 12.0, "contrast": 1e6,
+               "loads": np.array([[0.0, 0.0, 0.0, 0.0, 0.0, SQRT2]]), "precisions": ("fp64", "mixed"),
+               "workload": ("3D periodic cell, 256^3 trilinear hexes (8 Gauss points), the 512^3 recipe (smooth "
+                            "density, 32 Fourier modes, |k|<=12, E = 1/c + (1-1/c) rho^3, c = 1e6, nu 0.3, single "
+                            "load eps_xy = 1); Green-Jacobi PCG to 1e-8 relative residual; profiling stand-in for "
+                            "512^3")},
+}
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12   # SMs x max clock x FP64 flop/clk/SM (2 DFMA)
 ITER_COUNTS = os.path.join(ROOT, "oracle", "data", "iters_2d_1024.json")
 
@@ -786,7 +797,7 @@ def main():
         density, one warm-up solve, one timed solve (CUDA events on the solver's stream, L2
         flushed before), one profiled solve (per-kernel CUDA events) for the roofline."""
         from synthetic import smooth_density_device
-        cfg = CONFIGS_3D[key]
+        cfg = CONFIGS_3D[key] if key in CONFIGS_3D else PROFILE_CONFIGS_3D[key]
         shape = cfg["shape"]
         rho3 = smooth_density_device(shape, cfg["modes"], cfg["kmax"], SEED)
         rho3_h = rho3.cpu().numpy()

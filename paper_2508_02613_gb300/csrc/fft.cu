@@ -12,6 +12,34 @@ __global__ void k_twiddles(double2* tw, int n) {
   }
 }
 
+// Stage tables of the FP64 fused-multiply-add engine for line length L (first stage of
+// radix RM, later ones as StageRadix): slot NS - RM + e NS + k holds (c, t) of W_{R NS}^q,
+// q = lf_exponent(R, NS, e, k), for every stage of span NS >= RM, R = min(RM, L / NS);
+// c = cos(2 pi q / (R NS)), t = Im / c; where the cosine is zero (w = +-i), c = 2^-60 and
+// c t = +-1 exactly, the cosine's share then below 2^-60 |b|.
+static_assert(radix_max<double>() == kFftRadix64, "stage-table size of the plan");
+__global__ void k_lf_table(double2* dst, int L) {
+  constexpr int RM = radix_max<double>();
+  for (int NS = RM; NS < L;) {
+    const int R = L / NS >= RM ? RM : L / NS;
+    for (int i = threadIdx.x; i < (R - 1) * NS; i += blockDim.x) {
+      const int e = i / NS, k = i % NS;
+      const int q = lf_exponent(R, NS, e, k);
+      double s, c;
+      sincospi(-2.0 * (double)q / (double)(R * NS), &s, &c);
+      if (c == 0.0) c = 0x1p-60;
+      dst[NS - RM + i] = make_double2(c, s / c);
+    }
+    NS *= R;
+  }
+}
+
+cudaError_t launch_lf_table(double2* dst, int L, cudaStream_t st) {
+  if (L <= radix_max<double>()) return cudaErrorInvalidValue;
+  JFFT_K("lf_table", st, k_lf_table<<<1, 256, 0, st>>>(dst, L));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_twiddles(double2* tw, int n, cudaStream_t st) {
   JFFT_K("twiddles", st, k_twiddles<<<(n + 255) / 256, 256, 0, st>>>(tw, n));
   return cudaGetLastError();

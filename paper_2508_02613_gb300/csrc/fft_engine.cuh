@@ -125,6 +125,68 @@ template <typename T, bool INV> struct Dft<T, 16, INV> {
   }
 };
 
+// Fused multiply-add butterflies for the twiddled stages of the FP64 compile-time
+// engine (Linzer and Feig, "Modified FFTs for fused multiply-add architectures", Math.
+// Comp. 60 (1993)): a twiddle w = c (1 + i t), c = Re w, t = Im w / Re w, turns
+// a +- w b into u = b (1 + i t) (two FMAs) and a +- c u (two FMAs per output): six FP64
+// instructions where a complex multiply and two complex adds take eight. A radix-R
+// stage runs as log2 R radix-2 decimation-in-time layers, each with its own twiddles
+// (R - 1 per index k, in the slots of the plain stage's table). Same accuracy as the
+// plain form: |w b| rounds relative to |b| in both.
+template <typename T, bool INV> __device__ __forceinline__ void lf_bfly(cplx<T>& a, cplx<T>& b, cplx<T> w) {
+  const T t = INV ? -w.y : w.y;
+  const T ux = fma(-t, b.y, b.x), uy = fma(t, b.x, b.y);
+  const cplx<T> p = mk<T>(fma(w.x, ux, a.x), fma(w.x, uy, a.y));
+  b = mk<T>(fma(-w.x, ux, a.x), fma(-w.x, uy, a.y));
+  a = p;
+}
+
+// Exponent q of the layer twiddle W_{R NS}^q in slot e of index k (stage of span NS,
+// radix R): the lowest layer pairs (x_c, x_{c + R/2}) with W_{2 NS}^k, the next pairs the
+// results with W_{4 NS}^{k + NS m}, the top with W_{8 NS}^{k + NS m}, m = 0 .. R/2 - 1.
+__host__ __device__ inline int lf_exponent(int R, int NS, int e, int k) {
+  if (R == 2) return k;
+  if (R == 4) return e == 0 ? 2 * k : k + (e - 1) * NS;
+  if (e == 0) return 4 * k;
+  if (e <= 2) return 2 * k + (e - 1) * 2 * NS;
+  return k + (e - 3) * NS;
+}
+
+// x: the R stage inputs (positions b + r L / R), natural-order outputs on return; tk: the
+// slot of index k in the stage table, slot e at tk[e * NS].
+template <typename T, int R, bool INV, int NS>
+__device__ __forceinline__ void lf_stage(cplx<T>* x, const cplx<T>* __restrict__ tk) {
+  if constexpr (R == 2) {
+    lf_bfly<T, INV>(x[0], x[1], tk[0]);
+  } else if constexpr (R == 4) {
+    const cplx<T> w0 = tk[0];
+    lf_bfly<T, INV>(x[0], x[2], w0);   // x0 = E'0, x2 = E'1
+    lf_bfly<T, INV>(x[1], x[3], w0);   // x1 = O'0, x3 = O'1
+    lf_bfly<T, INV>(x[0], x[1], tk[NS]);       // X0, X2
+    lf_bfly<T, INV>(x[2], x[3], tk[2 * NS]);   // X1, X3
+    const cplx<T> x1 = x[1];
+    x[1] = x[2];
+    x[2] = x1;
+  } else {
+    static_assert(R == 8, "fused stages of radix 2, 4 or 8");
+    const cplx<T> w0 = tk[0], w1 = tk[NS], w2 = tk[2 * NS];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) lf_bfly<T, INV>(x[c], x[c + 4], w0);
+    // even subsequence: x0 / x4 (pair 0, 4) with x2 / x6 (pair 2, 6); odd: 1 / 5 with 3 / 7
+    lf_bfly<T, INV>(x[0], x[2], w1);   // E0, E2
+    lf_bfly<T, INV>(x[4], x[6], w2);   // E1, E3
+    lf_bfly<T, INV>(x[1], x[3], w1);   // O0, O2
+    lf_bfly<T, INV>(x[5], x[7], w2);   // O1, O3
+    lf_bfly<T, INV>(x[0], x[1], tk[3 * NS]);   // X0, X4
+    lf_bfly<T, INV>(x[4], x[5], tk[4 * NS]);   // X1, X5
+    lf_bfly<T, INV>(x[2], x[3], tk[5 * NS]);   // X2, X6
+    lf_bfly<T, INV>(x[6], x[7], tk[6 * NS]);   // X3, X7
+    const cplx<T> y[8] = {x[0], x[4], x[2], x[6], x[1], x[5], x[3], x[7]};
+#pragma unroll
+    for (int r = 0; r < 8; ++r) x[r] = y[r];
+  }
+}
+
 // One Stockham stage of radix R: each of the TPL lanes does RME / R butterflies.
 // FROM_REGS: inputs are v (stage 1 only, R == RME, positions j + TPL r).
 // tw: twiddle table exp(-2 pi i m / (L tws)) in shared memory (read with plain loads).
@@ -209,7 +271,9 @@ __device__ cplx<T>* line_fft(cplx<T>* v, int j, int L, cplx<T>* b0, cplx<T>* b1,
 // per-stage tables: the stage of span NS (> 1) and radix R keeps W_{NS R}^{r k}
 // (forward sign) at NS - RM + (r - 1) NS + k, k < NS, 1 <= r < R, L - RM entries in all.
 // Lanes read consecutive k there, where the strided reads of the axis table put up to
-// eight lanes of a warp on one shared-memory bank.
+// eight lanes of a warp on one shared-memory bank. FP64 runs the fused multiply-add
+// stages (lf_stage): the same slots hold (c, t) of W_{NS R}^{lf_exponent(R, NS, r - 1, k)},
+// built once per plan (k_lf_table).
 template <int RM, int L, int NS> struct StageRadix {
   static constexpr int R = (L / NS) >= RM ? RM : (L / NS);
 };
@@ -227,6 +291,18 @@ __device__ __forceinline__ void fill_stage_twiddles(cplx<T>* dst, const cplx<T>*
   }
 }
 
+// The block's per-stage tables: FP64 copies the plan's fused-form table (lf, L - RM
+// entries), FP32 gathers the plain twiddles from the axis table.
+template <typename T, int RM, int L, int TWS>
+__device__ __forceinline__ void stage_twiddles(cplx<T>* dst, const cplx<T>* __restrict__ tw_axis,
+                                               const cplx<T>* __restrict__ lf) {
+  if constexpr (sizeof(T) == 8) {
+    for (int i = threadIdx.x; i < L - RM; i += blockDim.x) dst[i] = lf[i];
+  } else {
+    fill_stage_twiddles<T, RM, L, TWS>(dst, tw_axis);
+  }
+}
+
 template <typename T, int RM, int R, bool INV, int L, int NS>
 __device__ __forceinline__ void fft_stage_ct(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int j,
                                              const cplx<T>* __restrict__ tst, T one) {
@@ -239,13 +315,17 @@ __device__ __forceinline__ void fft_stage_ct(const cplx<T>* __restrict__ src, cp
     cplx<T> x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = src[spad(b + r * step)];
+    if constexpr (sizeof(T) == 8) {
+      lf_stage<T, R, INV, NS>(x, tst + NS - RM + k);
+    } else {
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      cplx<T> w = tst[NS - RM + (r - 1) * NS + k];
-      if (INV) w.y = -w.y;
-      x[r] = c_mul<T>(x[r], w);
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tst[NS - RM + (r - 1) * NS + k];
+        if (INV) w.y = -w.y;
+        x[r] = c_mul<T>(x[r], w);
+      }
+      Dft<T, R, INV>::run(x, one);
     }
-    Dft<T, R, INV>::run(x, one);
     const int base = (b - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[spad(base + r * NS)] = x[r];

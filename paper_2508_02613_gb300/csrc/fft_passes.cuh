@@ -91,9 +91,9 @@ template <typename T> struct XrUpdate {
 template <typename T, bool REAL, bool JAC, bool XR, int LC>
 __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_rows_fwd(int D, const T* __restrict__ rin, const cplx<T>* __restrict__ cin,
                                                   cplx<T>* __restrict__ out, int R, int Lin, int lgTPL, int lgw,
-                                                  const cplx<T>* __restrict__ tw, const T* __restrict__ js,
-                                                  JScaleT<T> jsc, const CgState* __restrict__ cg, int slabs_per_b,
-                                                  XrUpdate<T> xr) {
+                                                  const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ lft,
+                                                  const T* __restrict__ js, JScaleT<T> jsc,
+                                                  const CgState* __restrict__ cg, int slabs_per_b, XrUpdate<T> xr) {
   using C = cplx<T>;
   constexpr int RM = radix_max<T>();
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
     const int npost = REAL ? L / 2 + 1 : 0;
     for (int i = threadIdx.x; i < npost; i += blockDim.x) twl[i] = tw[i];
     tst = twl + npost;
-    fill_stage_twiddles<T, RM, LC, REAL ? 2 : 1>(tst, tw);
+    stage_twiddles<T, RM, LC, REAL ? 2 : 1>(tst, tw, lft);
   } else {
     for (int i = threadIdx.x; i < Lin; i += blockDim.x) twl[i] = tw[i];
   }
@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_ro
 // Block = D * TPL threads; lanes [a TPL, (a+1) TPL) transform component a.
 template <typename T, int D, bool GREEN, int LC>
 __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __restrict__ spec, int nlines, int L, int lgTPL,
-                                               const cplx<T>* __restrict__ tw, const T* __restrict__ G,
-                                               const CgState* __restrict__ cg) {
+                                               const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ lft,
+                                               const T* __restrict__ G, const CgState* __restrict__ cg) {
   using C = cplx<T>;
   constexpr int RM = radix_max<T>();
   constexpr int NCMP = D * (D + 1) / 2;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
   // twiddles (the axis table, or the per-stage tables of a compile-time length), ordered
   // by the engine's first barrier
   C* twl = sm2;
-  if constexpr (LC > 0) fill_stage_twiddles<T, RM, LC, 1>(twl, tw);
+  if constexpr (LC > 0) stage_twiddles<T, RM, LC, 1>(twl, tw, lft);
   else
     for (int i = threadIdx.x; i < L; i += blockDim.x) twl[i] = tw[i];
   C* A = sm2 + L;
@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(512, FftOcc<T>::lines) k_lines(cplx<T>* __rest
 template <typename T, bool REAL, bool JAC, bool MULTI, int LC>
 __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_cols_inv(int D, const cplx<T>* __restrict__ in, T* __restrict__ rout,
                                                   cplx<T>* __restrict__ cout, int R, int Lin, int lgTPL, int lgw,
-                                                  const cplx<T>* __restrict__ tw, const T* __restrict__ js,
-                                                  JScaleT<T> jsc, const T* __restrict__ rdot,
+                                                  const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ lft,
+                                                  const T* __restrict__ js, JScaleT<T> jsc, const T* __restrict__ rdot,
                                                   double* __restrict__ partial, CgState* __restrict__ cg,
                                                   int slabs_per_b, StageCtl sc) {
   using C = cplx<T>;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(FftOcc<T>::rows_threads, FftOcc<T>::rows) k_co
     const int npost = REAL ? L / 2 + 1 : 0;
     for (int i = threadIdx.x; i < npost; i += blockDim.x) twl[i] = tw[i];
     tst = twl + npost;
-    fill_stage_twiddles<T, RM, LC, REAL ? 2 : 1>(tst, tw);
+    stage_twiddles<T, RM, LC, REAL ? 2 : 1>(tst, tw, lft);
   } else {
     for (int i = threadIdx.x; i < ntw; i += blockDim.x) twl[i] = tw[i];
   }
@@ -505,7 +505,7 @@ static cudaError_t pass_rows_real_fwd(const Grid& g, const FftPlanT<T>& p, const
                            : nm<T>("fft_rows_real_fwd", "fft_rows_real_fwd_f32");
   JFFT_K(name, st,
          k<<<grid, w * tpl, smem, st>>>(g.d, fused ? nullptr : r, nullptr, p.T, R, Lin, ilog2(tpl), ilog2(w),
-                                        p.tw[g.d - 1], js, jsc, cg, g.d, xr));
+                                        p.tw[g.d - 1], p.lf[g.d - 1], js, jsc, cg, g.d, xr));
   if (fused && nparts) *nparts = grid.x * g.d;
   return cudaGetLastError();
 }
@@ -523,8 +523,8 @@ static cudaError_t pass_rows_cplx_fwd(const Grid& g, const FftPlanT<T>& p, int n
   JFFT_TRY(set_smem(k, smem));
   JScaleT<T> jsc = {};
   JFFT_K(nm<T>("fft_rows_cplx_fwd", "fft_rows_cplx_fwd_f32"), st,
-         k<<<grid, w * tpl, smem, st>>>(g.d, nullptr, p.T, p.U, R, Lin, ilog2(tpl), ilog2(w), p.tw[1], nullptr, jsc, cg,
-                                        g.d * (g.M + 1), XrUpdate<T>{}));
+         k<<<grid, w * tpl, smem, st>>>(g.d, nullptr, p.T, p.U, R, Lin, ilog2(tpl), ilog2(w), p.tw[1], p.lf[1], nullptr,
+                                        jsc, cg, g.d * (g.M + 1), XrUpdate<T>{}));
   return cudaGetLastError();
 }
 
@@ -541,11 +541,11 @@ static cudaError_t pass_lines(const Grid& g, const FftPlanT<T>& p, int nb, bool 
   if (g.d == 2) {
     auto k = green ? lines_kernel<T, 2, true>(L) : lines_kernel<T, 2, false>(L);
     JFFT_TRY(set_smem(k, smem));
-    JFFT_K(name, st, k<<<grid, 2 * tpl, smem, st>>>(spec, nlines, L, ilog2(tpl), p.tw[0], p.G, cg));
+    JFFT_K(name, st, k<<<grid, 2 * tpl, smem, st>>>(spec, nlines, L, ilog2(tpl), p.tw[0], p.lf[0], p.G, cg));
   } else {
     auto k = green ? lines_kernel<T, 3, true>(L) : lines_kernel<T, 3, false>(L);
     JFFT_TRY(set_smem(k, smem));
-    JFFT_K(name, st, k<<<grid, 3 * tpl, smem, st>>>(spec, nlines, L, ilog2(tpl), p.tw[0], p.G, cg));
+    JFFT_K(name, st, k<<<grid, 3 * tpl, smem, st>>>(spec, nlines, L, ilog2(tpl), p.tw[0], p.lf[0], p.G, cg));
   }
   return cudaGetLastError();
 }
@@ -563,8 +563,8 @@ static cudaError_t pass_cols_cplx_inv(const Grid& g, const FftPlanT<T>& p, int n
   JFFT_TRY(set_smem(k, smem));
   JScaleT<T> jsc = {};
   JFFT_K(nm<T>("fft_cols_cplx_inv", "fft_cols_cplx_inv_f32"), st,
-         k<<<grid, w * tpl, smem, st>>>(g.d, p.U, nullptr, p.T, R, Lin, ilog2(tpl), ilog2(w), p.tw[1], nullptr, jsc, nullptr,
-                                        nullptr, cg, g.d * (g.M + 1), no_stage()));
+         k<<<grid, w * tpl, smem, st>>>(g.d, p.U, nullptr, p.T, R, Lin, ilog2(tpl), ilog2(w), p.tw[1], p.lf[1], nullptr,
+                                        jsc, nullptr, nullptr, cg, g.d * (g.M + 1), no_stage()));
   return cudaGetLastError();
 }
 
@@ -584,8 +584,8 @@ static cudaError_t pass_cols_real_inv(const Grid& g, const FftPlanT<T>& p, T* z,
                  : (jac ? cols_kernel<T, true, true, false>(L) : cols_kernel<T, true, false, false>(L));
   JFFT_TRY(set_smem(k, smem));
   JFFT_K(nm<T>("fft_cols_real_inv", "fft_cols_real_inv_f32"), st,
-         k<<<grid, w * tpl, smem, st>>>(g.d, p.T, z, nullptr, R, L + 1, ilog2(tpl), ilog2(w), p.tw[g.d - 1], js, jsc, r,
-                                        partial, cg, g.d, sc));
+         k<<<grid, w * tpl, smem, st>>>(g.d, p.T, z, nullptr, R, L + 1, ilog2(tpl), ilog2(w), p.tw[g.d - 1],
+                                        p.lf[g.d - 1], js, jsc, r, partial, cg, g.d, sc));
   if (nparts) *nparts = grid.x * g.d;
   return cudaGetLastError();
 }

@@ -36,6 +36,7 @@ struct jfft_solver {
   // device workspace
   double *field = nullptr, *E = nullptr, *esum = nullptr, *js = nullptr, *G = nullptr;
   double2* tw[3] = {nullptr, nullptr, nullptr};
+  double2* lf[3] = {nullptr, nullptr, nullptr};  // FP64 fused-form FFT stage tables (FftPlanT::lf)
   double2 *T = nullptr, *U = nullptr;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;
   double *partial = nullptr, *red = nullptr;
@@ -340,6 +341,10 @@ static int js_components(const Grid& g, int element) {
   return 1;
 }
 
+// Line length of the FFT passes along axis a: n_a, the last axis its half length (the
+// real passes' complex line).
+static int lf_length(const Grid& g, int a) { return a == g.d - 1 ? g.n[a] / 2 : g.n[a]; }
+
 // Device workspace of a solver (bytes), as allocated by jfft_create.
 static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int element = 0, int material_bf16 = 0) {
   const int d = g.d;
@@ -350,6 +355,8 @@ static size_t plan_bytes(const Grid& g, int ds, int nbmax, int precision, int el
   total += (3 + jsn) * g.N * sizeof(double);                        // field, E, esum, J^1/2 table
   total += (size_t)g.F * ds * sizeof(double);                       // G
   for (int a = 0; a < d; ++a) total += (size_t)g.n[a] * sizeof(double2);
+  for (int a = 0; a < d; ++a)                                       // fused-form stage tables
+    if (lf_length(g, a) > kFftRadix64) total += (size_t)(lf_length(g, a) - kFftRadix64) * sizeof(double2);
   total += (size_t)spec_n * sizeof(double2) * (d == 3 ? 2 : 1);     // T (U)
   total += 5 * (size_t)nbmax * fe * sizeof(double);                 // x r p q z
   total += (size_t)nbmax * 6 * kMaxPartials * sizeof(double);       // partial sums
@@ -641,6 +648,8 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
   AL(h->js, g.N * sizeof(double) * js_components(g, h->element));
   AL(h->G, (size_t)g.F * h->ds * sizeof(double));
   for (int a = 0; a < d; ++a) AL(h->tw[a], (size_t)g.n[a] * sizeof(double2));
+  for (int a = 0; a < d; ++a)
+    if (lf_length(g, a) > kFftRadix64) AL(h->lf[a], (size_t)(lf_length(g, a) - kFftRadix64) * sizeof(double2));
   AL(h->T, (size_t)spec_n * sizeof(double2));
   if (d == 3) AL(h->U, (size_t)spec_n * sizeof(double2));
   AL(h->x, (size_t)nbmax * fe * sizeof(double));
@@ -683,6 +692,7 @@ extern "C" jfft_status jfft_create(jfft_solver** out, const jfft_grid* grid, con
 
   for (int a = 0; a < d; ++a) {
     ce = launch_twiddles(h->tw[a], g.n[a], h->st);
+    if (ce == cudaSuccess && h->lf[a]) ce = launch_lf_table(h->lf[a], lf_length(g, a), h->st);
     if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "twiddles"));
   }
   s = setup_material(h, mat, false);
@@ -758,10 +768,11 @@ template <typename T> struct Work {
 };
 
 static Work<double> work64(jfft_solver* h) {
-  return {h->x, h->r, h->p, h->q, h->z, h->E, h->js, {{h->tw[0], h->tw[1], h->tw[2]}, h->T, h->U, h->G}};
+  return {h->x, h->r, h->p, h->q, h->z, h->E, h->js,
+          {{h->tw[0], h->tw[1], h->tw[2]}, {h->lf[0], h->lf[1], h->lf[2]}, h->T, h->U, h->G}};
 }
 static Work<float> work32(jfft_solver* h) {
-  return {h->x32, h->r32, h->p32, h->q32, h->z32, h->E32, h->js32, {{h->tw32[0], h->tw32[1], h->tw32[2]}, h->T32,
+  return {h->x32, h->r32, h->p32, h->q32, h->z32, h->E32, h->js32, {{h->tw32[0], h->tw32[1], h->tw32[2]}, {}, h->T32,
                                                                     h->U32, h->G32}};
 }
 

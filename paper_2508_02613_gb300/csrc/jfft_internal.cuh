@@ -203,10 +203,17 @@ cudaError_t launch_green_table(const Grid& g, const double* R, int64_t fstride, 
 cudaError_t launch_green_export(const Grid& g, const double* G, double* out, double scale_store, cudaStream_t st);
 
 // S6: twiddle table exp(-2 pi i m / n), m < n.
+// First-stage radix of the FP64 FFT engine; the fused-form stage table of a line of
+// length L > kFftRadix64 holds L - kFftRadix64 entries (launch_lf_table builds it).
+constexpr int kFftRadix64 = 8;
+cudaError_t launch_lf_table(double2* dst, int L, cudaStream_t st);
 cudaError_t launch_twiddles(double2* tw, int n, cudaStream_t st);
 
 template <typename R> struct FftPlanT {
   const cplx<R>* tw[3];
+  // FP64: the fused-form stage tables of the lines along axis a (complex length n_a;
+  // the last axis: its half length, the real passes' line), NULL where unused
+  const cplx<R>* lf[3];
   cplx<R>* T;        // spectrum buffer (real-axis pass output)
   cplx<R>* U;        // second spectrum buffer (3D)
   const R* G;        // stored symbol table [F][d*]
