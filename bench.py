@@ -879,6 +879,24 @@ def main():
                         "tol": TOL, "grid": list(c["shape"]), "contrast": c["contrast"], "loads": c["nloads"]}
         return out
 
+    def fp64_probe_leg():
+        """The measured FP64 FMA rate beside the derived peak of the FP64 rooflines: the
+        probe library (paper_2508_02613_gb300/probe/fp64_fma.cu, built by build()) runs 8
+        blocks of 256 threads per SM, each thread 8 independent FMA chains of 16384 steps,
+        timed with CUDA events after one warm-up launch; an FMA counts as two flops."""
+        import ctypes
+        lib = ctypes.CDLL(os.path.join(ROOT, "paper_2508_02613_gb300", "probe", "libjfft_probe.so"))
+        blocks, threads, iters, chains = 152 * 8, 256, 16384, 8
+        ms = ctypes.c_float(0.0)
+        torch.cuda.synchronize()
+        st = lib.jfft_probe_fp64_fma(blocks, threads, iters, ctypes.byref(ms))
+        if st != 0:
+            return {"error": f"cudaError {st}"}
+        tflops = blocks * threads * chains * iters * 2 / (ms.value / 1e3) / 1e12
+        return {"tflops": tflops, "ms": ms.value, "derived_peak_tflops": FP64_PEAK_TFLOPS,
+                "ratio_to_derived": tflops / FP64_PEAK_TFLOPS,
+                "shape": f"{blocks} x {threads} threads, {chains} chains x {iters} FMAs each"}
+
     def cufft_leg():
         """Timing cross-check only; cuFFT (through torch.fft) is on no path of the solver. The
         forward real 2D transform and its inverse of the fields one 1024^2 preconditioner
@@ -983,6 +1001,7 @@ def main():
                 if prec in ("mixed", "mixed_bf16"):
                     legs_3d[key][prec]["err_vs_oracle"] = err_vs_oracle("mixed", prec == "mixed_bf16", ("3d_16",))
     cufft_line = cufft_leg() if not args.no_cufft else None
+    fp64_probe_line = fp64_probe_leg()
     cells_line = cells_leg() if not args.no_cells else None
     serving_line = serving_leg() if not args.no_serving else None
 
@@ -1054,7 +1073,8 @@ def main():
                        "launch_shapes": "plan-time autotuner (options.autotune)"},
             "roofline": roof, "cpu_baseline": cpu_line, "cpu_openmp_baseline": cpu_omp_line, "e2e": e2e,
             "gpu_launches": launches // args.steps,
-            "clocks": clk, "mixed": mixed_line, "configs_3d": legs_3d, "cufft_crosscheck": cufft_line,
+            "clocks": clk, "fp64_fma_probe": fp64_probe_line, "mixed": mixed_line, "configs_3d": legs_3d,
+            "cufft_crosscheck": cufft_line,
             "small_cells": cells_line,
             "serving": serving_line,
             "detail": {"iters": {f"{pc}@{c:g}": v for (c, pc), v in iters.items()},
