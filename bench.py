@@ -962,8 +962,9 @@ def main():
     # ---- e2e through the C ABI with host buffers (FP64, the value's configuration)
     e2e = None
     if not args.no_e2e:
+        # the options of the timed FP64 leg (plan-time autotuner included), with host buffers
         sh = Solver(SHAPE, rho_h, NU, kind="density", e_min=1.0 / CONTRASTS[0], e_max=1.0, exponent=EXPONENT,
-                    stream=stream.cuda_stream, io="host", max_loads=N_LOADS, pinned=True)
+                    stream=stream.cuda_stream, io="host", max_loads=N_LOADS, pinned=True, autotune=True)
         rho_pin = torch.empty(SHAPE, dtype=torch.float64, pin_memory=True).numpy()
         rho_pin[...] = rho_h
         h2d = d2h = 0

@@ -5,6 +5,8 @@
 #include "element.cuh"
 #include "reduce.cuh"
 #include <cuda_bf16.h>
+#include <map>
+#include <mutex>
 
 namespace jfft {
 
@@ -120,8 +122,8 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
   const int t1 = blockIdx.x % mg.tiles1, t2 = blockIdx.x / mg.tiles1;
   const int i1s = t1 * mg.P1, i2s = (D == 3 ? t2 * mg.P2 : 0);
   const int L0 = blockIdx.y * mg.seg;
-  const int W1 = mg.P1 + 2, W2 = (D == 3 ? mg.P2 + 2 : 1);   // halo tile dims (nodes)
-  const int E1 = mg.P1 + 1, E2 = (D == 3 ? mg.P2 + 1 : 1);   // element tile dims
+  const int W2 = (D == 3 ? mg.P2 + 2 : 1);   // halo tile width along axis 2 (nodes)
+  const int E2 = (D == 3 ? mg.P2 + 1 : 1);   // element tile width along axis 2
   const T* xb = HAS_X ? x + (int64_t)b * fstride : nullptr;
   T* yb = y + (int64_t)b * fstride;
   StrainShift sh;
@@ -218,6 +220,48 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
   }
 }
 
+// Node layers [seg_begin(i, S, n0), seg_begin(i + 1, S, n0)) along axis 0 form segment i
+// of S for the marching kernels (lengths n0 / S rounded down or up).
+__host__ __device__ inline int seg_begin(int i, int S, int n0) { return (int)((int64_t)i * n0 / S); }
+
+// Segments per (column group, load) of a marching launch: n0 / seg for the requested
+// length; where the launch spans more than one wave of resident blocks, the count that
+// fills a whole number of waves instead (the nearest, rounded down so that no block starts
+// a last, nearly empty wave: a launch of 1.14 waves left most SMs idle for its tail); never
+// more partial-sum slots than kMaxPartials. Resident blocks per SM from the occupancy
+// calculator, per (kernel, device), cached.
+template <typename K> static int march_segments(K* kern, int threads, int ctas_x, int nb, int n0, int seg) {
+  int S = std::max(1, n0 / seg);
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int64_t> cap_cache;
+    int64_t cap = 0;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto it = cap_cache.find({(const void*)kern, dev});
+      if (it != cap_cache.end()) {
+        cap = it->second;
+      } else {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) == cudaSuccess)
+          cap = (int64_t)sms * per_sm;
+        cudaGetLastError();
+        cap_cache[{(const void*)kern, dev}] = cap;
+      }
+    }
+    const int64_t per_seg = (int64_t)ctas_x * nb;
+    if (cap > 0 && per_seg * S > cap) {
+      const int64_t waves = (per_seg * S + cap / 2) / cap;
+      const int64_t s2 = waves * cap / per_seg;
+      if (s2 >= 1) S = (int)std::min<int64_t>(s2, n0);
+    }
+  }
+  if ((int64_t)ctas_x * S > kMaxPartials) S = std::max(1, kMaxPartials / ctas_x);
+  return S;
+}
+
 // 2D operator, warp-marching form (no shared memory, no block barriers). Lane l of
 // a warp owns node column c = c0 + l (mod n1, the contiguous axis) and walks `seg`
 // node rows along axis 0. Per element row e0 it holds the node values of rows e0
@@ -239,7 +283,7 @@ template <typename T> constexpr int k2d_warps() { return sizeof(T) == 8 ? 1 : 4;
 template <typename T, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, bool P1, typename TE = T>
 __global__ void __launch_bounds__(32 * k2d_warps<T>())
     k_apply_K2d(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
-                T* __restrict__ y, int64_t fstride, int seg, int groups, const StrainShift* __restrict__ shifts,
+                T* __restrict__ y, int64_t fstride, int groups, const StrainShift* __restrict__ shifts,
                 T sgn, double* __restrict__ partial, CgState* __restrict__ cg, StageCtl sc) {
   const int b = blockIdx.z;
   if (cg && cg[b].done) return;
@@ -255,7 +299,7 @@ __global__ void __launch_bounds__(32 * k2d_warps<T>())
   const int ocol = o % n1;
   const T* xb = x + (int64_t)b * fstride;
   T* yb = y + (int64_t)b * fstride;
-  const int L0 = blockIdx.y * seg;
+  const int L0 = seg_begin(blockIdx.y, gridDim.y, n0), L1 = seg_begin(blockIdx.y + 1, gridDim.y, n0);
   T dot = T(0);
   if (active_warp) {
     T lo[2], hi[2], rlo[2], rhi[2], carry[2];
@@ -276,7 +320,7 @@ __global__ void __launch_bounds__(32 * k2d_warps<T>())
       }
       if (HAS_E) En = eload<T>(E, (int64_t)row * n1 + c);
     }
-    for (int e0 = L0 - 1; e0 < L0 + seg; ++e0) {
+    for (int e0 = L0 - 1; e0 < L1; ++e0) {
       const T Ee = HAS_E ? En : e_uniform;
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
@@ -284,7 +328,7 @@ __global__ void __launch_bounds__(32 * k2d_warps<T>())
         rhi[a] = __shfl_down_sync(0xffffffffu, hi[a], 1);
         if (lane == 31) rhi[a] = nh[a];
       }
-      if (e0 + 1 < L0 + seg) {           // prefetch node row e0 + 2 and element row e0 + 1
+      if (e0 + 1 < L1) {                 // prefetch node row e0 + 2 and element row e0 + 1
         const int rn2 = (e0 + 2) & (n0 - 1);   // n0 is a power of two
         const int re1 = (e0 + 1) & (n0 - 1);
         if (HAS_X) {
@@ -336,18 +380,15 @@ static cudaError_t apply_K2d_t(const Grid& g, const ElemConstT<T>& ec, const TE*
                                StageCtl sc, const StrainShift* shifts = nullptr, T sgn = T(1)) {
   const int groups = (g.n[1] + kWarpStride - 1) / kWarpStride;
   const int ctas_x = (groups + k2d_warps<T>() - 1) / k2d_warps<T>();
-  int seg = std::min(g.n[0], g.tune[0] > 0 ? g.tune[0] : 16);
-  while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
-  dim3 grid(ctas_x, g.n[0] / seg, nb);
+  const int seg = std::min(g.n[0], g.tune[0] > 0 ? g.tune[0] : 16);
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
                      : DOT == 1 ? "apply_K"
                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
-  if (ec.elem == 1)
-    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true, TE><<<grid, 32 * k2d_warps<T>(), 0, st>>>(
-                         g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
-  else
-    JFFT_K(name, st, k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false, TE><<<grid, 32 * k2d_warps<T>(), 0, st>>>(
-                         g, ec, E, e_uniform, x, y, fstride, seg, groups, shifts, sgn, partial, cg, sc));
+  auto kern = ec.elem == 1 ? k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, true, TE>
+                           : k_apply_K2d<T, DOT, HAS_E, HAS_X, SHIFT, false, TE>;
+  const dim3 grid(ctas_x, march_segments(kern, 32 * k2d_warps<T>(), ctas_x, nb, g.n[0], seg), nb);
+  JFFT_K(name, st, kern<<<grid, 32 * k2d_warps<T>(), 0, st>>>(g, ec, E, e_uniform, x, y, fstride, groups, shifts, sgn,
+                                                               partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
@@ -395,7 +436,7 @@ constexpr int kColsPerWarp3s = 30;
 template <typename T, int J, int DOT, bool HAS_E, bool HAS_X, bool SHIFT, typename TE = T>
 __global__ void __launch_bounds__(32 * kWarpsPerCta3d, k3d_min_blocks<T>())
     k_apply_K3s(Grid g, ElemConstT<T> ec, const TE* __restrict__ E, T e_uniform, const T* __restrict__ x,
-                T* __restrict__ y, int64_t fstride, int seg, int groups2, int rowblocks,
+                T* __restrict__ y, int64_t fstride, int groups2, int rowblocks,
                 const StrainShift* __restrict__ shifts, T sgn, double* __restrict__ partial,
                 CgState* __restrict__ cg, StageCtl sc) {
   const int b = blockIdx.z;
@@ -414,7 +455,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta3d, k3d_min_blocks<T>())
   const bool writer = active_warp && lane >= 1 && lane <= kColsPerWarp3s && cu <= n2;
   const T* xb = x + (int64_t)b * fstride;
   T* yb = y + (int64_t)b * fstride;
-  const int L0 = blockIdx.y * seg;
+  const int L0 = seg_begin(blockIdx.y, gridDim.y, n0), L1 = seg_begin(blockIdx.y + 1, gridDim.y, n0);
   constexpr int R = J + 2;  // node rows j0 - 1 .. j0 + J
   T dot = T(0);
   if (active_warp) {
@@ -434,7 +475,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta3d, k3d_min_blocks<T>())
     for (int i = 0; i < J; ++i)
 #pragma unroll
       for (int a = 0; a < 3; ++a) carry[i][a] = T(0);
-    for (int e0 = L0 - 1; e0 < L0 + seg; ++e0) {
+    for (int e0 = L0 - 1; e0 < L1; ++e0) {
       const int64_t pb0 = (int64_t)(e0 & (n0 - 1)) * n1 * n2;
       const int64_t pb1 = (int64_t)((e0 + 1) & (n0 - 1)) * n1 * n2;
       // node row 0 of the sweep (j0 - 1): plane stage
@@ -542,14 +583,14 @@ static cudaError_t apply_K3s_t(const Grid& g, const ElemConstT<T>& ec, const TE*
   const int rowblocks = g.n[1] / J;
   const int warps = groups2 * rowblocks;
   const int ctas_x = (warps + kWarpsPerCta3d - 1) / kWarpsPerCta3d;
-  int seg = std::min(g.n[0], g.tune[1] > 0 ? g.tune[1] : JFFT_K3S_SEG);
-  while ((int64_t)ctas_x * (g.n[0] / seg) > kMaxPartials) seg *= 2;
-  dim3 grid(ctas_x, g.n[0] / seg, nb);
+  const int seg = std::min(g.n[0], g.tune[1] > 0 ? g.tune[1] : JFFT_K3S_SEG);
+  auto kern = k_apply_K3s<T, J, DOT, HAS_E, HAS_X, SHIFT, TE>;
+  const dim3 grid(ctas_x, march_segments(kern, 32 * kWarpsPerCta3d, ctas_x, nb, g.n[0], seg), nb);
   const char* name = sizeof(T) == 4 ? (DOT == 1 ? "apply_K_f32" : "apply_K_f32_plain")
                      : DOT == 1 ? "apply_K"
                      : (!HAS_X ? "apply_K_rhs" : (SHIFT ? "apply_K_residual" : (HAS_E ? "apply_K_plain" : "apply_K_ref")));
-  JFFT_K(name, st, k_apply_K3s<T, J, DOT, HAS_E, HAS_X, SHIFT, TE><<<grid, 32 * kWarpsPerCta3d, 0, st>>>(
-                       g, ec, E, e_uniform, x, y, fstride, seg, groups2, rowblocks, shifts, sgn, partial, cg, sc));
+  JFFT_K(name, st, kern<<<grid, 32 * kWarpsPerCta3d, 0, st>>>(g, ec, E, e_uniform, x, y, fstride, groups2, rowblocks,
+                                                              shifts, sgn, partial, cg, sc));
   if (nparts) *nparts = grid.x * grid.y;
   return cudaGetLastError();
 }
