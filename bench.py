@@ -883,17 +883,27 @@ def main():
         """The measured FP64 FMA rate beside the derived peak of the FP64 rooflines: the
         probe library (paper_2508_02613_gb300/probe/fp64_fma.cu, built by build()) runs 8
         blocks of 256 threads per SM, each thread 8 independent FMA chains of 16384 steps,
-        timed with CUDA events after one warm-up launch; an FMA counts as two flops."""
-        import ctypes
-        lib = ctypes.CDLL(os.path.join(ROOT, "paper_2508_02613_gb300", "probe", "libjfft_probe.so"))
+        timed with CUDA events after one warm-up launch; an FMA counts as two flops. It runs
+        in a process of its own: the probe library links its own CUDA runtime, and a second
+        runtime instance in this process broke CUDA graph teardown in the request server's
+        worker threads (a crash inside cuGraphDestroy)."""
         blocks, threads, iters, chains = 152 * 8, 256, 16384, 8
-        ms = ctypes.c_float(0.0)
-        torch.cuda.synchronize()
-        st = lib.jfft_probe_fp64_fma(blocks, threads, iters, ctypes.byref(ms))
+        code = ("import ctypes, sys; lib = ctypes.CDLL(sys.argv[1]); ms = ctypes.c_float(0.0); "
+                "st = lib.jfft_probe_fp64_fma(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), ctypes.byref(ms)); "
+                "print(st, ms.value)")
+        lib = os.path.join(ROOT, "paper_2508_02613_gb300", "probe", "libjfft_probe.so")
+        try:
+            r = subprocess.run([sys.executable, "-c", code, lib, str(blocks), str(threads), str(iters)],
+                               capture_output=True, text=True, timeout=300,
+                               env=dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(local))))
+            st, ms = r.stdout.split()[:2]
+            st, ms = int(st), float(ms)
+        except (subprocess.SubprocessError, ValueError, OSError) as e:
+            return {"error": f"probe did not run: {type(e).__name__}"}
         if st != 0:
             return {"error": f"cudaError {st}"}
-        tflops = blocks * threads * chains * iters * 2 / (ms.value / 1e3) / 1e12
-        return {"tflops": tflops, "ms": ms.value, "derived_peak_tflops": FP64_PEAK_TFLOPS,
+        tflops = blocks * threads * chains * iters * 2 / (ms / 1e3) / 1e12
+        return {"tflops": tflops, "ms": ms, "derived_peak_tflops": FP64_PEAK_TFLOPS,
                 "ratio_to_derived": tflops / FP64_PEAK_TFLOPS,
                 "shape": f"{blocks} x {threads} threads, {chains} chains x {iters} FMAs each"}
 
