@@ -224,12 +224,36 @@ __global__ void __launch_bounds__(384) k_apply_K(Grid g, MarchGeom mg, ElemConst
 // of S for the marching kernels (lengths n0 / S rounded down or up).
 __host__ __device__ inline int seg_begin(int i, int S, int n0) { return (int)((int64_t)i * n0 / S); }
 
+// Resident blocks per SM of a kernel launched with `threads` threads and no dynamic shared
+// memory: the occupancy calculator's arithmetic (registers allocated per warp in units of
+// 256, the SM's register, thread, block and shared-memory limits) from attribute queries
+// only. These queries are what the FFT passes already issue while a stream is captured
+// into a graph; the occupancy API, called on a kernel's first use inside a capture by a
+// server worker thread, preceded crashes in the graph's teardown. 0 if a query fails.
+static int resident_blocks_per_sm(const void* kern, int threads, int dev) {
+  cudaFuncAttributes fa = {};
+  int regs_sm = 0, thr_sm = 0, blk_sm = 0, smem_sm = 0;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+  int per_sm = std::min(blk_sm, thr_sm / (warps * 32));
+  per_sm = std::min(per_sm, regs_sm / (regs_warp * warps));
+  if (fa.sharedSizeBytes > 0) per_sm = std::min(per_sm, smem_sm / (int)fa.sharedSizeBytes);
+  return std::max(per_sm, 0);
+}
+
 // Segments per (column group, load) of a marching launch: n0 / seg for the requested
 // length; where the launch spans more than one wave of resident blocks, the count that
 // fills a whole number of waves instead (the nearest, rounded down so that no block starts
 // a last, nearly empty wave: a launch of 1.14 waves left most SMs idle for its tail); never
-// more partial-sum slots than kMaxPartials. Resident blocks per SM from the occupancy
-// calculator, per (kernel, device), cached.
+// more partial-sum slots than kMaxPartials. Resident blocks per (kernel, device) cached.
 template <typename K> static int march_segments(K* kern, int threads, int ctas_x, int nb, int n0, int seg) {
   int S = std::max(1, n0 / seg);
   int dev = 0;
@@ -243,10 +267,9 @@ template <typename K> static int march_segments(K* kern, int threads, int ctas_x
       if (it != cap_cache.end()) {
         cap = it->second;
       } else {
-        int sms = 0, per_sm = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) == cudaSuccess)
-          cap = (int64_t)sms * per_sm;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+          cap = (int64_t)sms * resident_blocks_per_sm((const void*)kern, threads, dev);
         cudaGetLastError();
         cap_cache[{(const void*)kern, dev}] = cap;
       }
