@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -206,8 +207,25 @@ static jfft_status sync(jfft_solver* h) {
   return JFFT_OK;
 }
 
+// Every CUDA graph capture, instantiation and destruction of the library runs under one
+// process-wide lock: solvers driven from several host threads (the request server's
+// workers) built and tore down their loop graphs concurrently, and the template graph's
+// destruction then crashed inside the driver now and then. Kernel launches and graph
+// replays stay concurrent; only the (rare) graph construction and teardown serialise.
+static std::recursive_mutex& graph_mutex() {
+  static std::recursive_mutex m;
+  return m;
+}
+
+static void destroy_exec(cudaGraphExec_t& exec) {
+  if (!exec) return;
+  std::lock_guard<std::recursive_mutex> lock(graph_mutex());
+  cudaGraphExecDestroy(exec);
+  exec = nullptr;
+}
+
 static void drop_graph(jfft_solver* h, jfft_solver::ChunkGraph& gr) {
-  if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  destroy_exec(gr.exec);
   gr.exec = nullptr;
   for (auto& pe : gr.events) {
     h->pool.push_back(pe.a);
@@ -282,11 +300,7 @@ static void free_all(jfft_solver* h) {
   h->red_h = nullptr;
   h->active_h = nullptr;
   for (auto& gr : h->graph) drop_graph(h, gr);
-  for (auto& lg : h->loop)
-    if (lg.exec) {
-      cudaGraphExecDestroy(lg.exec);
-      lg.exec = nullptr;
-    }
+  for (auto& lg : h->loop) destroy_exec(lg.exec);
   if (h->chunks_h) cudaFreeHost(h->chunks_h);
   h->chunks_h = nullptr;
   for (auto& pe : h->pend) { h->pool.push_back(pe.a); h->pool.push_back(pe.b); }
@@ -467,11 +481,7 @@ static jfft_status setup_material(jfft_solver* h, const jfft_material* m, bool f
     set_unit_material(h, m->nu);
     // captured graphs hold the element constants and Jacobi scales by value
     for (auto& gr : h->graph) drop_graph(h, gr);
-    for (auto& lg : h->loop)
-      if (lg.exec) {
-        cudaGraphExecDestroy(lg.exec);
-        lg.exec = nullptr;
-      }
+    for (auto& lg : h->loop) destroy_exec(lg.exec);
   }
   // a coarse geometry is staged in the E buffer and expanded into the voxel field
   double* dst = coarse ? h->E : h->field;
@@ -905,6 +915,7 @@ static cudaError_t pcg_chunk_launch(jfft_solver* h, const Work<T>& w, int nb, in
   if (!gr.exec || gr.nb != nb || gr.pc != pc || gr.tol != tol || gr.stop_mode != stop_mode ||
       gr.max_iter != h->max_iter || gr.chunk != chunk || gr.prof != h->profiling) {
     drop_graph(h, gr);
+    std::lock_guard<std::recursive_mutex> lock(graph_mutex());
     cudaGraph_t graph = nullptr;
     const int64_t l0 = h->launches;
     const size_t p0 = h->pend.size();  // timing events recorded inside the capture belong to the graph
@@ -954,8 +965,8 @@ static bool loop_graph_ready(jfft_solver* h, const Work<T>& w, int nb, int pc, d
   if (lg.exec && lg.nb == nb && lg.pc == pc && lg.tol == tol && lg.stop_mode == stop_mode &&
       lg.max_iter == h->max_iter && lg.chunk == chunk)
     return true;
-  if (lg.exec) cudaGraphExecDestroy(lg.exec);
-  lg.exec = nullptr;
+  std::lock_guard<std::recursive_mutex> lock(graph_mutex());
+  destroy_exec(lg.exec);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaGraphCreate(&graph, 0);
   cudaGraphConditionalHandle cond = 0;
@@ -987,8 +998,7 @@ static bool loop_graph_ready(jfft_solver* h, const Work<T>& w, int nb, int pc, d
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    if (lg.exec) cudaGraphExecDestroy(lg.exec);
-    lg.exec = nullptr;
+    destroy_exec(lg.exec);
     h->loop_ok = false;
     return false;
   }
@@ -1479,11 +1489,7 @@ extern "C" jfft_status jfft_set_tuning(jfft_solver* h, const int* tune) {
   for (int i = 0; i < 4; ++i) h->g.tune[i] = tune[i];
   // captured graphs hold the old launch shapes
   for (auto& gr : h->graph) drop_graph(h, gr);
-  for (auto& lg : h->loop)
-    if (lg.exec) {
-      cudaGraphExecDestroy(lg.exec);
-      lg.exec = nullptr;
-    }
+  for (auto& lg : h->loop) destroy_exec(lg.exec);
   return JFFT_OK;
 }
 
