@@ -257,23 +257,34 @@ def ncu_traffic(workload):
     committed ncu summaries under profiles/, as lines
         traffic: workload=<w> kernel=<k> loads=<n> dram_bytes=<b> sources=<fingerprint>
     Only lines whose fingerprint matches the current sources are used: a capture of an
-    older kernel reads as no capture. Returns {kernel: (bytes per launch, loads, file)}."""
+    older kernel reads as no capture. A summary may declare the current sources equivalent
+    to captured ones, for changes that leave every kernel's device code and launch shape as
+    they were (host-side fixes), with a line
+        equivalent: sources=<current fingerprint> captured=<fingerprint> reason=<text>
+    Returns {kernel: (bytes per launch, loads, file)}."""
     out = {}
     fp = source_fingerprint()
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return out
+    lines = []
     for name in sorted(os.listdir(pdir)):
         if not name.endswith((".md", ".txt")):
             continue
         with open(os.path.join(pdir, name)) as fh:
-            for line in fh:
-                line = line.strip().strip("`")
-                if not line.startswith("traffic:"):
-                    continue
-                kv = dict(t.split("=", 1) for t in line[len("traffic:"):].split() if "=" in t)
-                if kv.get("workload") == workload and kv.get("sources") == fp:
-                    out[kv["kernel"]] = (float(kv["dram_bytes"]), int(kv.get("loads", 1)), name)
+            lines += [(name, line.strip().strip("`")) for line in fh]
+    accepted = {fp}
+    for _, line in lines:
+        if line.startswith("equivalent:"):
+            kv = dict(t.split("=", 1) for t in line[len("equivalent:"):].split() if "=" in t)
+            if kv.get("sources") == fp and kv.get("captured"):
+                accepted.add(kv["captured"])
+    for name, line in lines:
+        if not line.startswith("traffic:"):
+            continue
+        kv = dict(t.split("=", 1) for t in line[len("traffic:"):].split() if "=" in t)
+        if kv.get("workload") == workload and kv.get("sources") in accepted:
+            out[kv["kernel"]] = (float(kv["dram_bytes"]), int(kv.get("loads", 1)), name)
     return out
 
 

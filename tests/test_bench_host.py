@@ -28,6 +28,20 @@ def test_traffic_lines_need_the_current_fingerprint(tmp_path, monkeypatch):
     assert bench.ncu_traffic("w3") == {}
 
 
+def test_traffic_lines_of_declared_equivalent_sources(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "a.md").write_text("traffic: workload=w1 kernel=fft_lines loads=3 dram_bytes=1000 sources=old1\n"
+                               "traffic: workload=w1 kernel=cg_p loads=3 dram_bytes=700 sources=old2\n")
+    (prof / "eq.md").write_text("equivalent: sources=new0 captured=old1 reason=host-only\n"
+                                "equivalent: sources=other captured=old2 reason=not-this-tree\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_fingerprint", lambda: "new0")
+    assert bench.ncu_traffic("w1") == {"fft_lines": (1000.0, 3, "a.md")}
+    monkeypatch.setattr(bench, "source_fingerprint", lambda: "new1")
+    assert bench.ncu_traffic("w1") == {}
+
+
 def test_fingerprint_changes_with_a_kernel_source(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_2508_02613_gb300" / "csrc"
     csrc.mkdir(parents=True)
