@@ -227,9 +227,8 @@ __host__ __device__ inline int seg_begin(int i, int S, int n0) { return (int)((i
 // Resident blocks per SM of a kernel launched with `threads` threads and no dynamic shared
 // memory: the occupancy calculator's arithmetic (registers allocated per warp in units of
 // 256, the SM's register, thread, block and shared-memory limits) from attribute queries
-// only. These queries are what the FFT passes already issue while a stream is captured
-// into a graph; the occupancy API, called on a kernel's first use inside a capture by a
-// server worker thread, preceded crashes in the graph's teardown. 0 if a query fails.
+// only, the queries the FFT pass launchers also issue while a stream is being captured
+// into a graph (a kernel's first use is often inside such a capture). 0 if a query fails.
 static int resident_blocks_per_sm(const void* kern, int threads, int dev) {
   cudaFuncAttributes fa = {};
   int regs_sm = 0, thr_sm = 0, blk_sm = 0, smem_sm = 0;
