@@ -288,20 +288,25 @@ def ncu_traffic(workload):
     return out
 
 
-def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_steps=1):
+def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_steps=1, every=False):
     """Dominant kernel with its achieved rate, from the per-kernel CUDA events (summed event
     time per kernel name) of a profiling pass that repeats the timed work. Units are
     right-hand-side applications: per load, one operator and one preconditioner per PCG
     iteration; ``n_units`` of them in the profiled pass. ``alu``: report against the FP64
-    ALU peak derived from the unit counts (FP64 kernels), else against measured HBM."""
+    ALU peak derived from the unit counts (FP64 kernels), else against measured HBM.
+    ``every``: the same object for every kernel with a byte and flop model, largest share
+    first (a list)."""
     rows = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda r: -r[2])
+    found = []
     total_ms = sum(r[2] for r in rows)
     peak_gbs, peak_kind = hbm_peak_gbs()
     captured = ncu_traffic(workload)
     for name, nl, tot in rows:
         byt = traffic_bytes_per_unit(name, shape, material_bytes)
         fl = flops_per_unit(name, shape)
-        if byt is None or fl is None:
+        # the dominant kernel needs both models; the list also takes byte-only kernels
+        # (vectors) on HBM-bound legs
+        if byt is None or (fl is None and (alu or not every)):
             continue
         out = {"kernel": name, "launches": nl, "avg_launch_ms": tot / nl, "share": tot / total_ms,
                "units": n_units, "algorithmic_bytes_per_unit": byt, "algorithmic_flops_per_unit": fl,
@@ -314,7 +319,7 @@ def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_
         else:
             out["traffic_note"] = "no ncu capture of the current kernel sources for this workload"
         gbs = n_units * byt / (tot / 1e3) / 1e9
-        tfl = n_units * fl / (tot / 1e3) / 1e12
+        tfl = n_units * fl / (tot / 1e3) / 1e12 if fl is not None else None
         if alu:
             out.update({"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": tfl / FP64_PEAK_TFLOPS, "hbm_GBps_algorithmic": gbs,
@@ -322,8 +327,10 @@ def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_
         else:
             out.update({"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs,
                         "peak_note": f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"})
-        return out
-    return None
+        if not every:
+            return out
+        found.append(out)
+    return found if every else None
 
 
 def aggregate(ms_local, world, solves_per_step, dist=None, device=None):
@@ -979,6 +986,10 @@ def main():
     prof = fp64["prof"]
     n_units_fp64 = sum(sum(r["iters"]) for r in fp64["rec"].values()) * PROFILED_STEPS
     roof = roofline(prof, n_units_fp64, SHAPE, fp64["precision"] == "fp64", "2d_1024_sweep")
+    # the same for every modelled kernel of the leg (the dominant one is `roofline`)
+    roof_all = [{k: r[k] for k in ("kernel", "share", "bound", "achieved", "unit", "frac", "traffic")}
+                for r in roofline(prof, n_units_fp64, SHAPE, fp64["precision"] == "fp64", "2d_1024_sweep",
+                                  every=True)]
 
     # ---- e2e through the C ABI with host buffers (FP64, the value's configuration)
     e2e = None
@@ -1032,6 +1043,9 @@ def main():
         "dtype": "f32 inner PCG (operator, FFT, preconditioner, vectors) + f64 scalars, residual and solution",
         "roofline": roofline(mixed["prof"], sum(sum(r["iters"]) for r in mixed["rec"].values()) * PROFILED_STEPS,
                              SHAPE, False, "2d_1024_sweep_mixed"),
+        "roofline_kernels": [{k: r[k] for k in ("kernel", "share", "bound", "achieved", "unit", "frac", "traffic")}
+                             for r in roofline(mixed["prof"], sum(sum(r["iters"]) for r in mixed["rec"].values())
+                                               * PROFILED_STEPS, SHAPE, False, "2d_1024_sweep_mixed", every=True)],
         "clocks": mixed["clocks"], "gpu_launches": mixed["launches"] // args.steps,
         "time_to_tol_ms": {f"{pc}@{c:g}": round(v["ms"], 3) for (c, pc), v in mixed["rec"].items()},
         "iters": {f"{pc}@{c:g}": v["iters"] for (c, pc), v in mixed["rec"].items()},
@@ -1093,7 +1107,8 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MiB buffer written before each timed step (outside the timed interval)",
                        "launch_shapes": "plan-time autotuner (options.autotune)"},
-            "roofline": roof, "cpu_baseline": cpu_line, "cpu_openmp_baseline": cpu_omp_line, "e2e": e2e,
+            "roofline": roof, "roofline_kernels": roof_all, "cpu_baseline": cpu_line,
+            "cpu_openmp_baseline": cpu_omp_line, "e2e": e2e,
             "gpu_launches": launches // args.steps,
             "clocks": clk, "fp64_fma_probe": fp64_probe_line, "mixed": mixed_line, "configs_3d": legs_3d,
             "cufft_crosscheck": cufft_line,
