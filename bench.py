@@ -295,7 +295,9 @@ def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_
     iteration; ``n_units`` of them in the profiled pass. ``alu``: report against the FP64
     ALU peak derived from the unit counts (FP64 kernels), else against measured HBM.
     ``every``: the same object for every kernel with a byte and flop model, largest share
-    first (a list)."""
+    first (a list), limited to the kernels launched once per PCG iteration (at least half
+    as many launches as the dominant kernel): the setup and initial-residual kernels run
+    once per solve, so the per-iteration unit count does not apply to them."""
     rows = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda r: -r[2])
     found = []
     total_ms = sum(r[2] for r in rows)
@@ -329,7 +331,8 @@ def roofline(prof, n_units, shape, alu, workload, material_bytes=None, profiled_
                         "peak_note": f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"})
         if not every:
             return out
-        found.append(out)
+        if not found or nl >= 0.5 * found[0]["launches"]:
+            found.append(out)
     return found if every else None
 
 

@@ -92,3 +92,7 @@ def test_roofline_picks_the_dominant_kernel(monkeypatch):
     assert alu["bound"] == "alu" and alu["traffic"] is None
     assert alu["achieved"] == pytest.approx(12 * bench.flops_per_unit("apply_K", shape) / 2.0e-3 / 1e12)
     assert alu["frac"] == pytest.approx(alu["achieved"] / bench.FP64_PEAK_TFLOPS)
+    every = bench.roofline(dict(prof, fft_rows_real_fwd_f32=(1, 0.5)), 30, shape, False, "w", every=True)
+    # once-per-solve kernels (one launch here) are left out of the per-iteration list
+    assert [r["kernel"] for r in every] == ["fft_lines_f32", "apply_K_f32", "cg_p_f32"]
+    assert every[0]["frac"] == pytest.approx(r["frac"]) and all(0 < x["frac"] for x in every)
